@@ -1,0 +1,139 @@
+"""Pins for the oracle PIE (Section 2.1), colouring, batched mode and Algorithm 3."""
+import numpy as np
+import pytest
+
+from oracle import coeffs, dft, pie
+from paper_2408_03532_gb300 import synth
+
+
+def _rand(shape, seed=0):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def test_full_update_is_the_modulus_projection():
+    """With w = 1 and beta = 1, one FULL update replaces the patch by P_M(z)
+    (Eq. 3), whose Fourier modulus is exactly d."""
+    n = 16
+    obj = _rand((24, 24), 1)
+    probe = np.ones((n, n), complex)
+    d = np.random.default_rng(2).random((n, n)) + 0.1
+    z = obj.copy()
+    pie.pie_update(z, probe, (3, 5), d, pie.full_transform(n, n), 1.0, 1.0)
+    assert np.allclose(np.abs(np.fft.fft2(z[3:3 + n, 5:5 + n])), d, rtol=1e-12, atol=1e-12)
+    # pixels outside the patch are untouched
+    mask = np.ones_like(obj, bool)
+    mask[3:3 + n, 5:5 + n] = False
+    assert np.array_equal(z[mask], obj[mask])
+
+
+def test_truth_is_a_fixed_point_and_phase_invariance():
+    """Noise-free data: Phi = 0 at the truth and the sweep leaves it in place, for
+    any global phase; the PFT sweep moves it only by the approximation error."""
+    P = synth.small_raster_problem()
+    obj, probe, pos = P["obj"], P["probe"], P["pos"]
+    d = pie.amplitudes(P["intensities"])
+    for ph in (1.0, np.exp(0.7j)):
+        z, phi = pie.pie_sweep(obj * ph, probe, pos, d, pie.full_transform(32, 32), 1.0)
+        assert phi < 1e-24 * np.sum(d ** 2) / len(pos)
+        assert pie.relative_change(z, obj * ph) < 1e-13
+        assert pie.nrmse(z, obj) < 1e-13
+    P1, P2 = coeffs.plan_2d(32, 32, 16, 16, 8, 8)
+    dc = pie.amplitudes(P["intensities"], 16)
+    z, phi = pie.pie_sweep(obj, probe, pos, dc, pie.pft_transform(P1, P2), 1.0)
+    assert pie.relative_change(z, obj) < 1e-6
+
+
+def test_partial_dft_update_is_low_band_projection():
+    """For the exact partial DFT, A^H A / (n1 n2) is the projector onto the kept
+    band, so the update changes only those frequencies of the patch and sets
+    their moduli to d^crop (w = 1, beta = 1)."""
+    n, M = 16, 8
+    obj = _rand((n, n), 3)
+    d = np.random.default_rng(4).random((M, M)) + 0.1
+    z = obj.copy()
+    pie.pie_update(z, np.ones((n, n), complex), (0, 0), d, pie.partial_dft_transform(n, n, M, M), 1.0, 1.0)
+    assert np.allclose(np.abs(dft.partial_dft2(z, M, M)), d, atol=1e-12)
+    full_old, full_new = np.fft.fft2(obj), np.fft.fft2(z)
+    keep = np.zeros((n, n), bool)
+    idx = np.mod(np.arange(-M // 2, M // 2), n)
+    keep[np.ix_(idx, idx)] = True
+    assert np.allclose(full_new[~keep], full_old[~keep], atol=1e-11)
+
+
+def test_colouring_is_valid_and_greedy():
+    pos = synth.fermat_scan(256, 32, 200)
+    col = pie.greedy_colouring(pos, 32, 32)
+    for j in range(len(pos)):
+        for i in range(j):
+            if pie.overlaps(pos[i], pos[j], 32, 32):
+                assert col[i] != col[j]
+        # greedy: every smaller colour is taken by an earlier overlapping position
+        earlier = {int(col[i]) for i in range(j) if pie.overlaps(pos[i], pos[j], 32, 32)}
+        assert set(range(col[j])) <= earlier
+
+
+def test_order_within_a_colour_does_not_matter():
+    """Positions of one colour have disjoint patches, so permuting them inside
+    their colour gives exactly the same sweep."""
+    P = synth.small_raster_problem()
+    probe, pos = P["probe"], P["pos"]
+    d = pie.amplitudes(P["intensities"])
+    col = pie.greedy_colouring(pos, 32, 32)
+    order = pie.colour_major_order(col)
+    rng = np.random.default_rng(0)
+    shuffled = np.concatenate([rng.permutation(order[col[order] == c]) for c in range(col.max() + 1)])
+    T = pie.full_transform(32, 32)
+    z1, f1 = pie.pie_sweep(P["init"], probe, pos, d, T, 0.8, order)
+    z2, f2 = pie.pie_sweep(P["init"], probe, pos, d, T, 0.8, shuffled)
+    assert np.allclose(z1, z2, rtol=0, atol=1e-13)
+    assert f1 == pytest.approx(f2, rel=1e-12)
+
+
+def test_batched_equals_sequential_without_overlap():
+    """With disjoint patches and |w| = 1 the illumination is 1 on every patch, so
+    the batched update (delta = 0) equals the sequential one."""
+    n = 8
+    obj = _rand((32, 32), 5)
+    probe = np.exp(1j * np.random.default_rng(6).random((n, n)))
+    pos = synth.raster_scan(4, 4, 8, 0)
+    d = np.random.default_rng(7).random((16, n, n)) + 0.1
+    T = pie.full_transform(n, n)
+    zs, fs = pie.pie_sweep(obj, probe, pos, d, T, 0.9)
+    zb, fb = pie.batched_sweep(obj, probe, pos, d, T, 0.9, delta_rel=0.0)
+    assert np.allclose(zs, zb, atol=1e-13)
+    assert fs == pytest.approx(fb, rel=1e-12)
+
+
+def test_noise_free_recovery_up_to_global_phase():
+    """FULL PIE from a random start recovers a known object up to a global phase
+    on the well-lit region (noise-free data, known probe)."""
+    obj = synth.make_object(96)
+    probe = synth.make_probe(32)
+    pos = synth.fermat_scan(96, 32, 60)
+    d = pie.amplitudes(synth.simulate_intensities(obj, probe, pos))
+    il = pie.illumination(probe, pos, obj.shape)
+    mask = il >= 0.3 * il.max()
+    z = synth.random_init(96)
+    T = pie.full_transform(32, 32)
+    errs = []
+    for _ in range(80):
+        z, _ = pie.pie_sweep(z, probe, pos, d, T, 1.0)
+        errs.append(pie.nrmse(z, obj, mask))
+    assert errs[-1] < 1e-2
+    assert all(b <= a * 1.001 for a, b in zip(errs[10:], errs[11:]))
+    # the phase-free error of Eq. rel_error is no smaller than the aligned one
+    assert pie.relative_error(z[mask], obj[mask]) >= errs[-1] - 1e-15
+
+
+def test_hybrid_runs_both_phases_and_stops_on_tolerance():
+    """Algorithm 3: PFT sweeps on cropped data, then FULL sweeps; each phase
+    stops on its relative-change tolerance or its sweep budget."""
+    P = synth.small_raster_problem()
+    P1, P2 = coeffs.plan_2d(32, 32, 16, 16, 8, 8)
+    z, tr = pie.hybrid_pie(P["init"], P["probe"], P["pos"], P["intensities"], pie.pft_transform(P1, P2),
+                           16, 1.0, 1.0, 0.0, 4, 0.05, 30, truth=P["obj"])
+    phases = [t["phase"] for t in tr]
+    assert phases[:4] == ["pft"] * 4 and phases[4] == "full"
+    assert tr[-1]["change"] < 0.05 or len(tr) == 34
+    assert all("nrmse" in t for t in tr)
