@@ -1,0 +1,239 @@
+/*
+ * pft.h -- C ABI of the GB300 partial Fourier transform (PFT) and PIE library.
+ *
+ * The library implements, on one GPU (sm_103a):
+ *   - the 2-D fast partial Fourier transform of Parada, Wu Fung and Osher,
+ *     "Fast Partial Fourier Transforms for Large-Scale Ptychography"
+ *     (offline phase: Algorithm 4; online phase: Algorithm 5), which returns
+ *     the lowest M x M Fourier coefficients of each n x n frame, and its exact
+ *     adjoint;
+ *   - the exact partial DFT (the Appendix-A 2-D DFT restricted to the lowest
+ *     M x M frequencies) and a full 2-D FFT, for the refine phase and as
+ *     baselines;
+ *   - the PIE sweep (Section 2.1, Eq. pie_update with the modulus projection
+ *     of Eq. 3), run with either the PFT or the full FFT, and the hybrid
+ *     warm start of Algorithm 3;
+ *   - the gradient of the amplitude loss through the PFT with respect to the
+ *     object and the probe.
+ *
+ * Conventions (every call):
+ *   - Complex arrays are interleaved single precision (real, imaginary),
+ *     8 bytes per element, row-major. Real arrays are float.
+ *   - "device" pointers are CUDA device memory owned by the caller; "host"
+ *     pointers are ordinary host memory owned by the caller. The library never
+ *     frees caller memory. Plans and contexts are opaque, owned by the library,
+ *     and hold the tables, schedules and workspace they allocate.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Calls that take a stream enqueue work on it and return without
+ *     synchronising unless documented otherwise.
+ *   - The transform is unnormalised and uses e^{-2 pi i t k / n}. Output
+ *     frequencies are centred: row index t1 + M1/2, column t2 + M2/2, with
+ *     t in [-M/2, M/2 - 1]. The adjoint is the exact conjugate transpose of the
+ *     operator the plan applies (unscaled).
+ *   - Every call returns an int status: PFT_OK (0) or a negative PFT_ERR_*.
+ *     On error outputs are unspecified; pft_last_error() returns a
+ *     thread-local message. No C++ exception crosses the ABI.
+ */
+#ifndef PFT_GB300_H
+#define PFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PFT_OK                0
+#define PFT_ERR_INVALID_ARG  (-1)  /* null pointer, bad size, bad enum           */
+#define PFT_ERR_UNSUPPORTED  (-2)  /* valid request outside the built kernels    */
+#define PFT_ERR_CUDA         (-3)  /* a CUDA runtime call failed                  */
+#define PFT_ERR_NONFINITE    (-4)  /* NaN or Inf met in data or a result norm     */
+#define PFT_ERR_TIMEOUT      (-5)  /* a device-side wait gave up (status word)    */
+#define PFT_ERR_OOM          (-6)  /* device or host allocation failed            */
+
+/* ---- enums ------------------------------------------------------------- */
+#define PFT_PATH_AUTO        0   /* choose the factorised PFT when supported     */
+#define PFT_PATH_FACTORISED  1   /* Algorithm 5 (polynomial factorisation)       */
+#define PFT_PATH_DIRECT      2   /* exact partial DFT (dense M x n per axis)     */
+
+#define PFT_PREC_FP32        0   /* FP32 CUDA-core arithmetic, FP32 accumulation */
+
+#define PIE_TRANSFORM_PFT    0   /* PIE with the plan's partial transform (M x M) */
+#define PIE_TRANSFORM_FULL   1   /* PIE with the full n x n FFT                   */
+
+#define PIE_MODE_COLOURED    0   /* sequential PIE, positions grouped in colours
+                                    of non-overlapping patches (exact PIE order) */
+#define PIE_MODE_BATCHED     1   /* all positions read the same object; updates
+                                    summed and divided by the illumination       */
+
+/* Last error message of the calling thread ("" if none). Never NULL. */
+const char* pft_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int pft_version(void);
+
+/* ---- offline phase (host only, no GPU needed) ---------------------------
+ * Section 3.1.1: best uniform approximation P_{r-1, xi}(x) = sum_j w_j x^j of
+ * e^{i pi x} on |x| <= xi, with the scope xi(eps, r) = sup{xi : error <= eps}.
+ * By symmetry w_j = i^j a_j with a_j real.
+ *
+ * pft_design_coefficients: for (eps, r) writes xi(eps, r) to *xi and the r
+ *   real values a_0..a_{r-1} to a[] (host array of length >= r), and the
+ *   uniform error of the polynomial on |x| <= xi to *err (may be NULL).
+ *   1 <= r <= 32, 0 < eps < 1. Thread-safe; results are cached.
+ * pft_choose_r: Algorithm 1 step 2, r = min{ r : xi(eps, r) >= ratio },
+ *   ratio = m~/p = M/(2p). Writes r to *r (INVALID_ARG if none <= 32).
+ */
+int pft_design_coefficients(double eps, int r, double* xi, double* a, double* err);
+int pft_choose_r(double eps, double ratio, int* r);
+
+/* ---- plans (Algorithm 4) --------------------------------------------------
+ * A plan fixes the frame size n1 x n2, the output size M1 x M2 and the
+ * factorisation n_nu = p_nu q_nu. It computes the coefficients on the host
+ * and the tables B_nu (q_nu x r_nu, real after taking i^j into W), W_nu
+ * (M_nu x r_nu) and the DFT twiddles on the GPU in FP64 with exact integer
+ * phase reduction, stored as FP32.
+ *
+ * pft_plan_create(out, n1, n2, M1, M2, p1, p2, eps, r1, r2, path, precision)
+ *   n_nu: frame sides; M_nu: output sides (even, M_nu <= n_nu);
+ *   p_nu: divisors of n_nu, 0 = auto (p = M/2, so m~/p = 1 as in Section 4);
+ *   eps: polynomial tolerance (Section 4 uses 1e-7); r_nu: 0 = Algorithm 1's
+ *   choice, else forced; path: PFT_PATH_*; precision: PFT_PREC_*.
+ *   Synchronises the device once (table generation). UNSUPPORTED when the
+ *   sizes are outside the built kernels (the message says which).
+ */
+typedef struct pft_plan pft_plan;
+
+typedef struct pft_plan_info {
+  int n1, n2, M1, M2;
+  int p1, p2, q1, q2, r1, r2;   /* factorisation and polynomial terms per axis */
+  double xi1, xi2;              /* scopes xi(eps, r_nu)                        */
+  double eps;
+  int path;                     /* PFT_PATH_FACTORISED or PFT_PATH_DIRECT      */
+  int precision;
+} pft_plan_info;
+
+int pft_plan_create(pft_plan** out, int n1, int n2, int M1, int M2, int p1, int p2,
+                    double eps, int r1, int r2, int path, int precision);
+int pft_plan_destroy(pft_plan* plan);
+int pft_plan_info_get(const pft_plan* plan, pft_plan_info* info);
+
+/* Copy the plan's FP32 tables to host memory (for inspection and tests).
+ * axis 0 or 1. B: q x r real (row-major, may be NULL); W: M x r complex
+ * (row-major, includes the factor i^j, may be NULL). */
+int pft_plan_tables(const pft_plan* plan, int axis, float* B, float* W);
+
+/* ---- online phase: batched transforms ------------------------------------
+ * pft_forward (Algorithm 5): x = device [batch][n1][n2] complex,
+ *   y = device [batch][M1][M2] complex (centred). x and y must not overlap.
+ * pft_adjoint: y = device [batch][M1][M2] -> x = device [batch][n1][n2],
+ *   x = A^H y for the plan's operator A (unscaled).
+ * batch >= 0 (0 is a no-op). Asynchronous on `stream`.
+ */
+int pft_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void* stream);
+int pft_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void* stream);
+
+/* ---- full FFT (baseline and refine phase) ---------------------------------
+ * pft_fft2: unnormalised full 2-D DFT of n x n frames (inverse = 0) or its
+ *   conjugate transpose (inverse = 1, i.e. n^2 times the inverse DFT);
+ *   in/out device [batch][n][n], may alias. n in {16, 32, 64, 128}.
+ * pft_fft_crop: full 2-D FFT of each n x n frame followed by the centred
+ *   M x M crop (the naive route the PFT avoids); out device [batch][M][M].
+ */
+int pft_fft2(const void* in, void* out, int n, int64_t batch, int inverse, void* stream);
+int pft_fft_crop(const void* in, void* out, int n, int M, int64_t batch, void* stream);
+
+/* ---- PIE ------------------------------------------------------------------
+ * A context holds one reconstruction problem: object size, probe, scan
+ * positions, measured intensities and the plans it needs.
+ *
+ * pie_ctx_create(out, problem, probe, positions, intensities, stream)
+ *   probe:       device [n][n] complex (copied; later changes to the caller's
+ *                buffer are not seen);
+ *   positions:   host int32 [N][2], top-left (row, col) of each n x n patch,
+ *                0 <= row <= obj_h - n, 0 <= col <= obj_w - n;
+ *   intensities: device float [N][n][n], far-field intensities in FFT order
+ *                (not shifted). The context stores d = sqrt(I) and the
+ *                centred crop d^crop (Algorithm 3, step 1).
+ *   Synchronises `stream` once. The caller's buffers may be freed afterwards.
+ */
+typedef struct pie_ctx pie_ctx;
+
+typedef struct pie_problem {
+  int obj_h, obj_w;      /* object size                                       */
+  int n;                 /* probe / frame side                                 */
+  int npos;              /* N, number of scan positions                        */
+  int M;                 /* PFT output side (even, <= n)                       */
+  int p;                 /* PFT divisor (0 = auto, M/2)                        */
+  double eps;            /* PFT polynomial tolerance (0 = 1e-7)                */
+  int mode;              /* PIE_MODE_*                                         */
+  int path;              /* PFT_PATH_* for the partial transform               */
+  double delta_rel;      /* batched mode: delta = delta_rel * max illumination */
+} pie_problem;
+
+typedef struct pie_stats {
+  double phi;            /* (1/N) sum_j ||R_j||^2 / n^2 during the sweep (Eq. 4) */
+  double rel_change;     /* ||z_new - z_old|| / ||z_old||  (Section 4)           */
+} pie_stats;
+
+int pie_ctx_create(pie_ctx** out, const pie_problem* problem, const void* probe,
+                   const int32_t* positions, const float* intensities, void* stream);
+int pie_ctx_destroy(pie_ctx* ctx);
+
+/* Number of colours of the greedy colouring (positions in index order take
+ * the smallest colour unused by an earlier overlapping patch), and the
+ * colour of each position (host int32 [N], may be NULL). */
+int pie_ctx_colours(const pie_ctx* ctx, int* ncolours, int32_t* colour_of);
+
+/* One PIE sweep over all positions (Eq. pie_update with Eq. 3), in place on
+ * `object` (device [obj_h][obj_w] complex). transform: PIE_TRANSFORM_*.
+ * Step: beta * conj(w) / max|w|^2 (coloured) or
+ * beta * conj(w) / (illumination + delta) (batched). For the PFT the
+ * residual step is A^H(A psi - d^crop sgn(A psi)) / n^2.
+ * If `stats` is non-NULL the call synchronises `stream` and fills it
+ * (FP64 reductions on the GPU); with NULL it stays asynchronous. */
+int pie_iteration(pie_ctx* ctx, void* object, int transform, double beta,
+                  pie_stats* stats, void* stream);
+
+/* Algorithm 3: PFT sweeps until rel_change < tol_pft or max_pft sweeps, then
+ * full-FFT sweeps until rel_change < tol_full or max_full sweeps.
+ * truth: optional device [obj_h][obj_w] complex; with it each trace entry also
+ * holds the phase-aligned error on the illuminated mask (pixels with
+ * illumination >= 1e-3 of its maximum). trace: host array with room for
+ * max_pft + max_full entries (may be NULL); *ntrace receives the count.
+ * Synchronises `stream` after every sweep (the stopping rule reads norms). */
+typedef struct pie_schedule {
+  double beta_pft, beta_full;
+  double tol_pft, tol_full;
+  int max_pft, max_full;
+} pie_schedule;
+
+typedef struct pie_trace {
+  int phase;             /* PIE_TRANSFORM_PFT or PIE_TRANSFORM_FULL */
+  double phi, rel_change, nrmse;
+  double seconds;        /* wall time since the call started        */
+} pie_trace;
+
+int warm_start_then_refine(pie_ctx* ctx, void* object, const pie_schedule* schedule,
+                           const void* truth, pie_trace* trace, int* ntrace, void* stream);
+
+/* Phase-aligned error min_phi ||e^{i phi} z - truth|| / ||truth|| over the
+ * context's illuminated mask (FP64 on the GPU); synchronises `stream`. */
+int pie_nrmse(pie_ctx* ctx, const void* object, const void* truth, double* out, void* stream);
+
+/* Amplitude loss through the context's partial transform A:
+ *   L = sum_j || |A(w . Q_j z)| - d_j^crop ||^2,
+ * with gradients in the convention dL/dRe + i dL/dIm:
+ *   grad_obj   device [obj_h][obj_w] complex (overwritten),
+ *   grad_probe device [n][n] complex (overwritten, may be NULL),
+ * for the given object and probe (device, not modified). The exit waves are
+ * recomputed per position, not stored. *loss (host) is written after a
+ * synchronisation of `stream`. */
+int pie_amp_loss_grad(pie_ctx* ctx, const void* object, const void* probe, void* grad_obj,
+                      void* grad_probe, double* loss, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFT_GB300_H */

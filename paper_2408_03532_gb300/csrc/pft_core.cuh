@@ -1,0 +1,167 @@
+// Device building blocks of the factorised PFT (Algorithm 5) on sm_103a.
+//
+// A 2-D PFT is separable: z^ = A1 Z A2^T with each A_nu an M x n operator of
+// the 1-D form of Algorithm 2, so a frame is transformed row by row (axis 2)
+// into an n x M intermediate Y and then column by column (axis 1).
+//
+// One 1-D transform of a length-n vector (n = P Q) runs on a group of P lanes
+// of a warp; lane k owns the block x[Q k .. Q k + Q - 1]:
+//   stage A (Algorithm 2 line 2, C = Z B): C[k][j] = sum_l B[l][j] x[Q k + l],
+//     with B[l][j] = a_j (1 - 2 l / Q)^j real. Rows l and Q - l have opposite
+//     abscissae, so even j use x_l + x_{Q-l} and odd j use x_l - x_{Q-l},
+//     halving the multiply-adds. B sits in the kernel's parameter space and
+//     every index is a compile-time constant, so it is read as a constant
+//     operand of the FMA instructions.
+//   stage B (lines 3-6): a P-point DFT over k for each j, done across the P
+//     lanes by a radix-2 butterfly network with shuffles (lane k then holds
+//     residue v = bitrev(k)), followed by
+//     z^[t] = sum_j W'[t][j] C^[t mod P][j] for the M/P outputs t = v mod P,
+//     where W'[t][j] = i^j (t/P)^j e^{-i pi t/P} carries the factor i^j of
+//     w_j = i^j a_j.
+// The adjoint runs the exact transpose of each step in reverse order.
+#pragma once
+
+#include "common.cuh"
+
+namespace pftk {
+
+constexpr int RMAX = 13;       // polynomial terms the kernels are built for (r <= 13)
+constexpr int BH_ROWS = 17;    // Q/2 + 1 rows of B kept (Q <= 32)
+
+// Per-plan constants passed by value (kernel parameter space).
+struct PftConst {
+  float bh[2][BH_ROWS][RMAX];  // [axis][l][j] = a_j (1 - 2l/Q)^j, l = 0..Q/2
+};
+
+// Column slot -> column index: places the columns that share a half-warp at
+// indices that differ in bits log2(P)..3, so that with the XOR swizzle below
+// the column reads of one half-warp hit 16 different bank pairs.
+template <int P>
+__device__ __forceinline__ int col_of(int cs) {
+  if (P >= 16) return cs;
+  constexpr int C = P >= 16 ? 1 : 16 / P;  // columns per half-warp
+  int base = cs & ~15, r = cs & 15;
+  return base | ((r % C) * P + r / C);
+}
+
+// Row-major n x M intermediate with row stride M + 8 and an XOR swizzle of the
+// column by the row's block index (u / Q) & 15: row writes stay a permutation
+// of one row, column reads of one block-column spread over all banks.
+template <int Q, int M>
+struct YLayout {
+  static constexpr int S = M + 8;
+  __device__ __forceinline__ static int at(int u, int t) { return u * S + (t ^ ((u / Q) & 15)); }
+};
+
+// ---------------------------------------------------------------- stage A
+template <int Q>
+__device__ __forceinline__ void stageA_fwd(const float2 (&x)[Q], float2 (&C)[RMAX],
+                                           const float (&bh)[BH_ROWS][RMAX]) {
+  constexpr int H = Q / 2;
+  float2 s[H > 1 ? H : 1], d[H > 1 ? H : 1];
+  float2 tot = cadd(x[0], x[H]);
+#pragma unroll
+  for (int l = 1; l < H; ++l) {
+    s[l] = cadd(x[l], x[Q - l]);
+    d[l] = csub(x[l], x[Q - l]);
+    tot = cadd(tot, s[l]);
+  }
+  C[0] = cscale(tot, bh[0][0]);
+#pragma unroll
+  for (int j = 1; j < RMAX; ++j) {
+    float2 acc = cscale(x[0], bh[0][j]);
+#pragma unroll
+    for (int l = 1; l < H; ++l) {
+      const float2 v = (j & 1) ? d[l] : s[l];
+      acc.x = fmaf(bh[l][j], v.x, acc.x);
+      acc.y = fmaf(bh[l][j], v.y, acc.y);
+    }
+    C[j] = acc;
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void stageA_adj(const float2 (&E)[RMAX], float2 (&x)[Q],
+                                           const float (&bh)[BH_ROWS][RMAX]) {
+  constexpr int H = Q / 2;
+  float2 x0 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < RMAX; ++j) {
+    x0.x = fmaf(bh[0][j], E[j].x, x0.x);
+    x0.y = fmaf(bh[0][j], E[j].y, x0.y);
+  }
+  x[0] = x0;
+  x[H] = cscale(E[0], bh[0][0]);  // abscissa 0: only j = 0
+#pragma unroll
+  for (int l = 1; l < H; ++l) {
+    float2 e = make_float2(0.f, 0.f), o = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+      if (j & 1) {
+        o.x = fmaf(bh[l][j], E[j].x, o.x);
+        o.y = fmaf(bh[l][j], E[j].y, o.y);
+      } else {
+        e.x = fmaf(bh[l][j], E[j].x, e.x);
+        e.y = fmaf(bh[l][j], E[j].y, e.y);
+      }
+    }
+    x[l] = cadd(e, o);
+    x[Q - l] = csub(e, o);
+  }
+}
+
+// ----------------------------------------------------------- 1-D transform
+template <int P, int Q, int MP>
+struct Pft1D {
+  static constexpr int N = P * Q;
+  static constexpr int M = MP * P;
+
+  // index of the first output of lane k's residue (outputs are c P + w, c < MP)
+  __device__ __forceinline__ static int first_out(int k) { return (bitrev<P>(k) + M / 2) % P; }
+
+  // Forward: lane k holds x[Qk .. Qk+Q-1]; calls store(t_idx, value) for the
+  // outputs t_idx (= t + M/2) of its residue. sW: [RMAX][M] (j-major).
+  template <class Store>
+  __device__ __forceinline__ static void forward(const float2 (&x)[Q], int k,
+                                                 const float (&bh)[BH_ROWS][RMAX],
+                                                 const float2* __restrict__ sW,
+                                                 const float2* __restrict__ twp, Store store) {
+    float2 C[RMAX];
+    stageA_fwd<Q>(x, C, bh);
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) C[j] = lane_dif<P, false>(C[j], k, twp);
+    const int w = first_out(k);
+#pragma unroll
+    for (int c = 0; c < MP; ++c) {
+      const int t = c * P + w;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) acc = cfma(acc, sW[j * M + t], C[j]);
+      store(t, acc);
+    }
+  }
+
+  // Adjoint: load(t_idx) returns the input at output index t_idx of lane k's
+  // residue; on exit x[l] = (A^H y)[Qk + l].
+  template <class Load>
+  __device__ __forceinline__ static void adjoint(Load load, int k,
+                                                 const float (&bh)[BH_ROWS][RMAX],
+                                                 const float2* __restrict__ sW,
+                                                 const float2* __restrict__ twp, float2 (&x)[Q]) {
+    const int w = first_out(k);
+    float2 yv[MP];
+#pragma unroll
+    for (int c = 0; c < MP; ++c) yv[c] = load(c * P + w);
+    float2 E[RMAX];
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc = cfmac(acc, sW[j * M + c * P + w], yv[c]);
+      E[j] = lane_dif_adj<P, false>(acc, k, twp);
+    }
+    stageA_adj<Q>(E, x, bh);
+  }
+};
+
+}  // namespace pftk

@@ -1,0 +1,770 @@
+// PIE on the GPU: one fused kernel per scan position computes
+//   psi = w . Q_j z                         (exit wave, Eq. 1)
+//   Psi = A psi                             (PFT of Algorithm 5, or the full FFT)
+//   R = Psi - d_j . sgn(Psi)                (modulus projection residual, Eq. 3)
+//   dpsi = A^H R / n^2                      (= psi - P_M(psi) for A = F)
+//   z_j <- z_j - beta conj(w) / max|w|^2 . dpsi   (Eq. pie_update)
+// and accumulates ||R||^2 for the objective of Eq. 4. Positions are grouped in
+// colours whose patches do not overlap; the colours run one after another, so a
+// sweep is exactly sequential PIE in colour-major order. The batched mode lets
+// all positions read the same object and sums their updates instead.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fft_core.cuh"
+#include "plan.cuh"
+
+using namespace pftk;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+enum { MODE_COLOURED = 0, MODE_BATCHED = 1, MODE_GRAD = 2 };
+
+struct PieArgs {
+  float2* obj;              // object [H][W] (read; written in MODE_COLOURED)
+  const float2* objr;       // object read pointer (= obj, or the gradient's input)
+  long long obj_w;
+  const float2* probe;      // [n][n]
+  const int2* pos;          // [N] top-left (row, col)
+  const int* list;          // positions to process (nullptr = 0..count-1)
+  int count;
+  const float* dat;         // amplitudes: [N][M][M] centred crop, or [N][n][n] FFT order
+  float coef;               // update scale
+  float2* acc;              // MODE_BATCHED: sum conj(w) dpsi; MODE_GRAD: grad_obj
+  float2* gprobe;           // MODE_GRAD: grad_probe (may be null)
+  double* red;              // red[0] += sum ||R||^2 (MODE_GRAD: loss)
+};
+
+// Modulus-projection residual (Eq. 3) and its contribution to the objective.
+template <int MODE>
+__device__ __forceinline__ float2 residual(float2 Psi, float d, double& acc) {
+  const float m2 = cabs2(Psi);
+  if (MODE == MODE_GRAD) {
+    // sgn(0) = 0; gradient of sum (|Psi| - d)^2 is 2 R
+    if (m2 > 0.f) {
+      const float m = sqrtf(m2);
+      const float diff = m - d;
+      acc += (double)diff * (double)diff;
+      return cscale(Psi, 2.f * diff / m);
+    }
+    acc += (double)d * (double)d;
+    return make_float2(0.f, 0.f);
+  }
+  // theta(0) = 0: a zero coefficient is replaced by d
+  float2 R;
+  if (m2 > 0.f) {
+    const float m = sqrtf(m2);
+    R = cscale(Psi, 1.f - d / m);
+  } else {
+    R = make_float2(-d, 0.f);
+  }
+  acc += (double)cabs2(R);
+  return R;
+}
+
+template <int MODE>
+__device__ __forceinline__ void apply_update(const PieArgs& a, long long oidx, float2 w, float2 dpsi, int pidx) {
+  if (MODE == MODE_COLOURED) {
+    float2 o = a.obj[oidx];
+    const float2 u = cmulc(dpsi, w);  // conj(w) dpsi
+    o.x = fmaf(-a.coef, u.x, o.x);
+    o.y = fmaf(-a.coef, u.y, o.y);
+    a.obj[oidx] = o;
+  } else if (MODE == MODE_BATCHED) {
+    atomicAdd(a.acc + oidx, cscale(cmulc(dpsi, w), a.coef));
+  } else {
+    atomicAdd(a.acc + oidx, cmulc(dpsi, w));
+    if (a.gprobe) atomicAdd(a.gprobe + pidx, cmulc(dpsi, a.objr[oidx]));
+  }
+}
+
+__device__ __forceinline__ void block_accumulate(double v, double* red_smem, double* out) {
+  double s = block_sum(v, red_smem);
+  if (threadIdx.x == 0 && s != 0.0) atomicAdd(out, s);
+}
+
+// ------------------------------------------------------ PFT position kernel
+template <int P, int Q, int MP>
+struct PieShape {
+  static constexpr int N = P * Q, M = MP * P, G = 32 / P;
+  using L = YLayout<Q, M>;
+  static constexpr int OFF_W1 = 0;
+  static constexpr int OFF_W2 = OFF_W1 + RMAX * M;
+  static constexpr int OFF_TW = OFF_W2 + RMAX * M;
+  static constexpr int OFF_Y = OFF_TW + 16;
+  static constexpr int ZS = M + 1;
+  static constexpr int OFF_Z = OFF_Y + N * L::S;
+  static constexpr int OFF_RED = OFF_Z + M * ZS;
+  static constexpr size_t SMEM = sizeof(float2) * (OFF_RED + kWarps);
+};
+
+template <int P, int Q, int MP, int MODE>
+__global__ void __launch_bounds__(kThreads) k_pie_pft(PieArgs a, const __grid_constant__ PftConst c,
+                                                      const float2* __restrict__ gW,
+                                                      const float2* __restrict__ gtw) {
+  using S = PieShape<P, Q, MP>;
+  using T = Pft1D<P, Q, MP>;
+  constexpr int N = S::N, M = S::M, G = S::G;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* sW1 = sm + S::OFF_W1;
+  float2* sW2 = sm + S::OFF_W2;
+  float2* stw = sm + S::OFF_TW;
+  float2* sY = sm + S::OFF_Y;
+  float2* sZ = sm + S::OFF_Z;
+  double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
+  for (int i = threadIdx.x; i < 2 * RMAX * M; i += kThreads) sm[i] = gW[i];
+  for (int i = threadIdx.x; i < P / 2; i += kThreads) stw[i] = gtw[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = lane % P, g = lane / P;
+  for (int it = blockIdx.x; it < a.count; it += gridDim.x) {
+    const int j = a.list ? a.list[it] : it;
+    const int2 rc = a.pos[j];
+    const long long obase = (long long)rc.x * a.obj_w + rc.y;
+    // rows: exit wave and axis-2 transform
+    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
+      const int u = u0 + g;
+      float2 xv[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const int v = Q * k + l;
+        xv[l] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
+      }
+      T::forward(xv, k, c.bh[1], sW2, stw, [&](int t, float2 val) { sY[S::L::at(u, t)] = val; });
+    }
+    __syncthreads();
+    for (int cs0 = warp * G; cs0 < M; cs0 += kWarps * G) {
+      const int t2 = col_of<P>(cs0 + g);
+      float2 xv[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) xv[l] = sY[S::L::at(Q * k + l, t2)];
+      T::forward(xv, k, c.bh[0], sW1, stw, [&](int t1, float2 val) { sZ[t1 * S::ZS + t2] = val; });
+    }
+    __syncthreads();
+    // modulus projection on the M x M coefficients
+    const float* dj = a.dat + (long long)j * (M * M);
+    double part = 0.0;
+    for (int i = threadIdx.x; i < M * M; i += kThreads) {
+      float2* z = sZ + (i / M) * S::ZS + (i % M);
+      *z = residual<MODE>(*z, __ldg(dj + i), part);
+    }
+    block_accumulate(part, sred, a.red);
+    __syncthreads();
+    // adjoint: columns then rows
+    for (int cs0 = warp * G; cs0 < M; cs0 += kWarps * G) {
+      const int t2 = col_of<P>(cs0 + g);
+      float2 xv[Q];
+      T::adjoint([&](int t1) { return sZ[t1 * S::ZS + t2]; }, k, c.bh[0], sW1, stw, xv);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) sY[S::L::at(Q * k + l, t2)] = xv[l];
+    }
+    __syncthreads();
+    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
+      const int u = u0 + g;
+      float2 xv[Q];
+      T::adjoint([&](int t) { return sY[S::L::at(u, t)]; }, k, c.bh[1], sW2, stw, xv);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const int v = Q * k + l;
+        apply_update<MODE>(a, obase + (long long)u * a.obj_w + v, __ldg(a.probe + u * N + v), xv[l], u * N + v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------- full-FFT position kernel
+template <int N, int MODE>
+__global__ void __launch_bounds__(kThreads) k_pie_full(PieArgs a, const float2* __restrict__ gtw) {
+  using F = Fft<N>;
+  constexpr int L = F::L, E = F::E, G = F::G, S = F::S;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm;
+  float2* sF = sm + N;
+  double* sred = reinterpret_cast<double*>(sF + N * S);
+  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = gtw[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l = lane % L, g = lane / L;
+  for (int it = blockIdx.x; it < a.count; it += gridDim.x) {
+    const int j = a.list ? a.list[it] : it;
+    const int2 rc = a.pos[j];
+    const long long obase = (long long)rc.x * a.obj_w + rc.y;
+    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
+      const int u = u0 + g;
+      float2 x[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = l + L * e;
+        x[e] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
+      }
+      F::fwd(x, l, tw);
+#pragma unroll
+      for (int p = 0; p < E; ++p) sF[u * S + p * L + l] = x[p];
+    }
+    __syncthreads();
+    for (int b0 = warp * G; b0 < N; b0 += kWarps * G) {
+      const int b = b0 + g;
+      float2 x[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) x[e] = sF[(l + L * e) * S + b];
+      F::fwd(x, l, tw);
+#pragma unroll
+      for (int p = 0; p < E; ++p) sF[(p * L + l) * S + b] = x[p];
+    }
+    __syncthreads();
+    const float* dj = a.dat + (long long)j * (N * N);
+    double part = 0.0;
+    for (int i = threadIdx.x; i < N * N; i += kThreads) {
+      const int sa = i / N, sb = i % N;
+      float2* z = sF + sa * S + sb;
+      *z = residual<MODE>(*z, __ldg(dj + F::freq_of_slot(sa) * N + F::freq_of_slot(sb)), part);
+    }
+    block_accumulate(part, sred, a.red);
+    __syncthreads();
+    for (int b0 = warp * G; b0 < N; b0 += kWarps * G) {
+      const int b = b0 + g;
+      float2 x[E];
+#pragma unroll
+      for (int p = 0; p < E; ++p) x[p] = sF[(p * L + l) * S + b];
+      F::adj(x, l, tw);
+#pragma unroll
+      for (int e = 0; e < E; ++e) sF[(l + L * e) * S + b] = x[e];
+    }
+    __syncthreads();
+    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
+      const int u = u0 + g;
+      float2 x[E];
+#pragma unroll
+      for (int p = 0; p < E; ++p) x[p] = sF[u * S + p * L + l];
+      F::adj(x, l, tw);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = l + L * e;
+        apply_update<MODE>(a, obase + (long long)u * a.obj_w + v, __ldg(a.probe + u * N + v), x[e], u * N + v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ helper kernels
+__global__ void k_amplitudes(const float* __restrict__ I, float* __restrict__ d, float* __restrict__ dc,
+                             int npos, int n, int M) {
+  const long long tot = (long long)npos * n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x)
+    d[i] = sqrtf(fmaxf(I[i], 0.f));
+  const long long totc = (long long)npos * M * M;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < totc; i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i / (M * M);
+    const int r = (int)(i % (M * M));
+    const int t1 = r / M - M / 2, t2 = r % M - M / 2;
+    const int f1 = (t1 % n + n) % n, f2 = (t2 % n + n) % n;
+    dc[i] = sqrtf(fmaxf(I[j * n * n + f1 * n + f2], 0.f));
+  }
+}
+
+__global__ void k_illumination(const float2* __restrict__ probe, const int2* __restrict__ pos, int npos, int n,
+                               long long W, float* __restrict__ illum) {
+  const long long tot = (long long)npos * n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(i / (n * n)), r = (int)(i % (n * n));
+    const int u = r / n, v = r % n;
+    const int2 rc = pos[j];
+    atomicAdd(illum + (long long)(rc.x + u) * W + rc.y + v, cabs2(probe[r]));
+  }
+}
+
+__global__ void k_max(const float* __restrict__ x, long long n, unsigned int* out) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, x[i]);
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(PFT_FULL_MASK, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // m >= 0
+}
+
+__global__ void k_finish_illum(float* __restrict__ illum, long long n, const unsigned int* __restrict__ mx,
+                               float delta_rel, unsigned char* __restrict__ mask) {
+  const float m = __uint_as_float(*mx);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float v = illum[i];
+    mask[i] = (m > 0.f && v >= 1e-3f * m) ? 1 : 0;
+    illum[i] = 1.f / (v + delta_rel * m);  // becomes the inverse illumination
+  }
+}
+
+// red[0] += sum |a - b|^2, red[1] += sum |b|^2   (FP64)
+__global__ void k_diff_norms(const float2* __restrict__ a, const float2* __restrict__ b, long long n, double* red) {
+  __shared__ double s[kWarps];
+  double d2 = 0.0, b2 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 x = a[i], y = b[i];
+    const double dx = (double)x.x - y.x, dy = (double)x.y - y.y;
+    d2 += dx * dx + dy * dy;
+    b2 += (double)y.x * y.x + (double)y.y * y.y;
+  }
+  double t = block_sum(d2, s);
+  if (threadIdx.x == 0) atomicAdd(red, t);
+  t = block_sum(b2, s);
+  if (threadIdx.x == 0) atomicAdd(red + 1, t);
+}
+
+// masked sums for the phase-aligned error: red += [Re <z,t>, Im <z,t>, |z|^2, |t|^2]
+__global__ void k_align_sums(const float2* __restrict__ z, const float2* __restrict__ t,
+                             const unsigned char* __restrict__ mask, long long n, double* red) {
+  __shared__ double s[kWarps];
+  double v[4] = {0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (!mask[i]) continue;
+    const double zr = z[i].x, zi = z[i].y, tr = t[i].x, ti = t[i].y;
+    v[0] += zr * tr + zi * ti;  // conj(z) t
+    v[1] += zr * ti - zi * tr;
+    v[2] += zr * zr + zi * zi;
+    v[3] += tr * tr + ti * ti;
+  }
+  for (int q = 0; q < 4; ++q) {
+    double tt = block_sum(v[q], s);
+    if (threadIdx.x == 0) atomicAdd(red + q, tt);
+  }
+}
+
+// z <- z - beta * acc * inv_illum  (batched update)
+__global__ void k_apply_batched(float2* __restrict__ z, const float2* __restrict__ acc,
+                                const float* __restrict__ inv_illum, float beta, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float s = beta * inv_illum[i];
+    float2 o = z[i];
+    const float2 u = acc[i];
+    o.x = fmaf(-s, u.x, o.x);
+    o.y = fmaf(-s, u.y, o.y);
+    z[i] = o;
+  }
+}
+
+// -------------------------------------------------------------- registries
+struct PftPieKernels {
+  int P, Q, MP;
+  const void* k[3];
+  size_t smem;
+};
+
+template <int P, int Q, int MP>
+PftPieKernels make_pft_pie() {
+  return PftPieKernels{P, Q, MP,
+                       {(const void*)k_pie_pft<P, Q, MP, MODE_COLOURED>, (const void*)k_pie_pft<P, Q, MP, MODE_BATCHED>,
+                        (const void*)k_pie_pft<P, Q, MP, MODE_GRAD>},
+                       PieShape<P, Q, MP>::SMEM};
+}
+
+const PftPieKernels g_pft_pie[] = {
+    make_pft_pie<8, 4, 2>(),  make_pft_pie<8, 8, 2>(),  make_pft_pie<16, 4, 2>(), make_pft_pie<8, 16, 2>(),
+    make_pft_pie<16, 8, 2>(), make_pft_pie<32, 4, 2>(), make_pft_pie<16, 16, 2>(), make_pft_pie<32, 8, 2>(),
+};
+
+struct FullPieKernels {
+  int N;
+  const void* k[3];
+  size_t smem;
+};
+
+template <int N>
+FullPieKernels make_full_pie() {
+  return FullPieKernels{N,
+                        {(const void*)k_pie_full<N, MODE_COLOURED>, (const void*)k_pie_full<N, MODE_BATCHED>,
+                         (const void*)k_pie_full<N, MODE_GRAD>},
+                        sizeof(float2) * (N + N * Fft<N>::S) + sizeof(double) * kWarps};
+}
+
+const FullPieKernels g_full_pie[] = {make_full_pie<16>(), make_full_pie<32>(), make_full_pie<64>(),
+                                     make_full_pie<128>()};
+
+int grid_for(long long work) {
+  long long g = (work + kThreads - 1) / kThreads;
+  long long cap = 8LL * pfth::sm_count();
+  return (int)std::max(1LL, std::min(g, cap));
+}
+
+}  // namespace
+
+struct pie_ctx {
+  pie_problem pb;
+  int n = 0, npos = 0, H = 0, W = 0, M = 0;
+  pft_plan plan;
+  bool have_plan = false;
+  int pft_kid = -1, full_kid = -1;
+  float2* d_probe = nullptr;
+  float probe_max2 = 0.f;
+  int2* d_pos = nullptr;
+  std::vector<int2> h_pos;
+  float* d_amp = nullptr;      // [N][n][n]
+  float* d_ampc = nullptr;     // [N][M][M]
+  std::vector<int> colour, col_off;
+  int ncol = 0;
+  int* d_sched = nullptr;
+  float* d_inv_illum = nullptr;
+  unsigned char* d_mask = nullptr;
+  float2* d_prev = nullptr;
+  float2* d_acc = nullptr;
+  double* d_red = nullptr;     // [8]
+  double* h_red = nullptr;     // pinned [8]
+  int per_sm[2][3] = {};       // occupancy of the PFT / full kernels per mode
+};
+
+namespace {
+
+int prepare_kernel(const void* fn, size_t smem, int* per_sm) {
+  PFT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PFT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, smem));
+  if (*per_sm < 1) return pfth::set_error(PFT_ERR_UNSUPPORTED, "PIE kernel does not fit on an SM");
+  return PFT_OK;
+}
+
+// Greedy colouring in index order (smallest colour unused by an earlier
+// overlapping patch); colour-major schedule, index order within a colour.
+void colour_positions(pie_ctx* c) {
+  const int N = c->npos, n = c->n;
+  c->colour.assign(N, -1);
+  // bucket positions by n x n cells so only neighbouring cells are scanned
+  const int cw = (c->W + n - 1) / n + 1, ch = (c->H + n - 1) / n + 1;
+  std::vector<std::vector<int>> cells((size_t)cw * ch);
+  std::vector<char> used;
+  int ncol = 0;
+  for (int j = 0; j < N; ++j) {
+    const int2 p = c->h_pos[j];
+    const int cx = p.y / n, cy = p.x / n;
+    used.assign(ncol + 1, 0);
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int yy = cy + dy, xx = cx + dx;
+        if (yy < 0 || xx < 0 || yy >= ch || xx >= cw) continue;
+        for (int i : cells[(size_t)yy * cw + xx]) {
+          const int2 q = c->h_pos[i];
+          if (std::abs(q.x - p.x) < n && std::abs(q.y - p.y) < n) used[c->colour[i]] = 1;
+        }
+      }
+    int col = 0;
+    while (col < ncol && used[col]) ++col;
+    c->colour[j] = col;
+    if (col == ncol) ++ncol;
+    cells[(size_t)cy * cw + cx].push_back(j);
+  }
+  c->ncol = ncol;
+  c->col_off.assign(ncol + 1, 0);
+  for (int j = 0; j < N; ++j) c->col_off[c->colour[j] + 1]++;
+  for (int k = 0; k < ncol; ++k) c->col_off[k + 1] += c->col_off[k];
+}
+
+int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) {
+  if (a.count <= 0) return PFT_OK;
+  if (transform == PIE_TRANSFORM_PFT) {
+    const PftPieKernels& K = g_pft_pie[c->pft_kid];
+    int grid = std::min(a.count, c->per_sm[0][mode] * pfth::sm_count());
+    PftConst cst = c->plan.cst;
+    const float2* W = c->plan.d_W;
+    const float2* tw = c->plan.d_twp;
+    void* args[] = {(void*)&a, (void*)&cst, (void*)&W, (void*)&tw};
+    PFT_CUDA_TRY(cudaLaunchKernel(K.k[mode], dim3(grid), dim3(kThreads), args, K.smem, st));
+  } else {
+    const FullPieKernels& K = g_full_pie[c->full_kid];
+    int grid = std::min(a.count, c->per_sm[1][mode] * pfth::sm_count());
+    const float2* tw = pfth::twiddles(c->n);
+    if (!tw) return PFT_ERR_CUDA;
+    void* args[] = {(void*)&a, (void*)&tw};
+    PFT_CUDA_TRY(cudaLaunchKernel(K.k[mode], dim3(grid), dim3(kThreads), args, K.smem, st));
+  }
+  return PFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pie_ctx_destroy(pie_ctx* c) {
+  if (!c) return PFT_OK;
+  if (c->have_plan) {
+    cudaFree(c->plan.d_W);
+    cudaFree(c->plan.d_twp);
+    cudaFree(c->plan.d_B);
+  }
+  cudaFree(c->d_probe);
+  cudaFree(c->d_pos);
+  cudaFree(c->d_amp);
+  cudaFree(c->d_ampc);
+  cudaFree(c->d_sched);
+  cudaFree(c->d_inv_illum);
+  cudaFree(c->d_mask);
+  cudaFree(c->d_prev);
+  cudaFree(c->d_acc);
+  cudaFree(c->d_red);
+  if (c->h_red) cudaFreeHost(c->h_red);
+  delete c;
+  return PFT_OK;
+}
+
+int pie_ctx_create(pie_ctx** out, const pie_problem* pb, const void* probe, const int32_t* positions,
+                   const float* intensities, void* stream) {
+  if (!out || !pb || !probe || !positions || !intensities)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const int n = pb->n, N = pb->npos, H = pb->obj_h, W = pb->obj_w, M = pb->M;
+  if (n <= 0 || N <= 0 || H < n || W < n) return pfth::set_error(PFT_ERR_INVALID_ARG, "bad problem sizes");
+  if (M <= 0 || M % 2 || M > n) return pfth::set_error(PFT_ERR_INVALID_ARG, "need even 0 < M <= n");
+  if (pb->mode != PIE_MODE_COLOURED && pb->mode != PIE_MODE_BATCHED)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown mode %d", pb->mode);
+  if (pb->path != PFT_PATH_AUTO && pb->path != PFT_PATH_FACTORISED)
+    return pfth::set_error(PFT_ERR_UNSUPPORTED, "PIE is built with the factorised PFT only");
+  cudaStream_t st = (cudaStream_t)stream;
+  pie_ctx* c = new (std::nothrow) pie_ctx();
+  if (!c) return pfth::set_error(PFT_ERR_OOM, "host allocation failed");
+  c->pb = *pb;
+  c->n = n; c->npos = N; c->H = H; c->W = W; c->M = M;
+  int rc = PFT_OK;
+#define PIE_TRY(x)                    \
+  do {                                \
+    rc = (x);                         \
+    if (rc != PFT_OK) {               \
+      pie_ctx_destroy(c);             \
+      return rc;                      \
+    }                                 \
+  } while (0)
+#define PIE_CUDA(x)                                                   \
+  do {                                                                \
+    cudaError_t e_ = (x);                                             \
+    if (e_ != cudaSuccess) {                                          \
+      rc = pfth::cuda_error(e_, #x);                                  \
+      pie_ctx_destroy(c);                                             \
+      return rc;                                                      \
+    }                                                                 \
+  } while (0)
+  // positions
+  c->h_pos.resize(N);
+  for (int j = 0; j < N; ++j) {
+    const int r = positions[2 * j], q = positions[2 * j + 1];
+    if (r < 0 || q < 0 || r > H - n || q > W - n) {
+      pie_ctx_destroy(c);
+      return pfth::set_error(PFT_ERR_INVALID_ARG, "position %d (%d, %d) outside the object", j, r, q);
+    }
+    c->h_pos[j] = make_int2(r, q);
+  }
+  // PFT plan and kernels
+  PIE_TRY(pfth::build_plan(&c->plan, n, M, pb->p, pb->eps > 0 ? pb->eps : 1e-7, 0));
+  c->have_plan = true;
+  for (int i = 0; i < (int)(sizeof(g_pft_pie) / sizeof(g_pft_pie[0])); ++i)
+    if (g_pft_pie[i].P == c->plan.p1 && g_pft_pie[i].Q == c->plan.q1 && g_pft_pie[i].MP == M / c->plan.p1)
+      c->pft_kid = i;
+  if (c->pft_kid < 0) {
+    pie_ctx_destroy(c);
+    return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for n=%d M=%d", n, M);
+  }
+  for (int i = 0; i < (int)(sizeof(g_full_pie) / sizeof(g_full_pie[0])); ++i)
+    if (g_full_pie[i].N == n) c->full_kid = i;
+  for (int m = 0; m < 3; ++m) {
+    PIE_TRY(prepare_kernel(g_pft_pie[c->pft_kid].k[m], g_pft_pie[c->pft_kid].smem, &c->per_sm[0][m]));
+    if (c->full_kid >= 0)
+      PIE_TRY(prepare_kernel(g_full_pie[c->full_kid].k[m], g_full_pie[c->full_kid].smem, &c->per_sm[1][m]));
+  }
+  if (c->full_kid >= 0 && !pfth::twiddles(n)) {
+    pie_ctx_destroy(c);
+    return PFT_ERR_CUDA;
+  }
+  // probe
+  std::vector<float2> hp((size_t)n * n);
+  PIE_CUDA(cudaMalloc(&c->d_probe, sizeof(float2) * n * n));
+  PIE_CUDA(cudaMemcpyAsync(c->d_probe, probe, sizeof(float2) * n * n, cudaMemcpyDeviceToDevice, st));
+  PIE_CUDA(cudaMemcpyAsync(hp.data(), probe, sizeof(float2) * n * n, cudaMemcpyDeviceToHost, st));
+  PIE_CUDA(cudaStreamSynchronize(st));
+  for (auto& v : hp) c->probe_max2 = std::max(c->probe_max2, v.x * v.x + v.y * v.y);
+  if (!(c->probe_max2 > 0.f) || !std::isfinite(c->probe_max2)) {
+    pie_ctx_destroy(c);
+    return pfth::set_error(PFT_ERR_NONFINITE, "probe is zero or not finite");
+  }
+  PIE_CUDA(cudaMalloc(&c->d_pos, sizeof(int2) * N));
+  PIE_CUDA(cudaMemcpyAsync(c->d_pos, c->h_pos.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, st));
+  // amplitudes
+  PIE_CUDA(cudaMalloc(&c->d_amp, sizeof(float) * (size_t)N * n * n));
+  PIE_CUDA(cudaMalloc(&c->d_ampc, sizeof(float) * (size_t)N * M * M));
+  k_amplitudes<<<grid_for((long long)N * n * n), kThreads, 0, st>>>(intensities, c->d_amp, c->d_ampc, N, n, M);
+  PIE_CUDA(cudaGetLastError());
+  // colouring
+  colour_positions(c);
+  std::vector<int> sched(N);
+  {
+    std::vector<int> fill(c->col_off.begin(), c->col_off.end() - 1);
+    for (int j = 0; j < N; ++j) sched[fill[c->colour[j]]++] = j;
+  }
+  PIE_CUDA(cudaMalloc(&c->d_sched, sizeof(int) * N));
+  PIE_CUDA(cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  // illumination, inverse illumination, mask
+  const long long HW = (long long)H * W;
+  PIE_CUDA(cudaMalloc(&c->d_inv_illum, sizeof(float) * HW));
+  PIE_CUDA(cudaMalloc(&c->d_mask, HW));
+  PIE_CUDA(cudaMalloc(&c->d_prev, sizeof(float2) * HW));
+  PIE_CUDA(cudaMalloc(&c->d_red, sizeof(double) * 8));
+  PIE_CUDA(cudaMallocHost(&c->h_red, sizeof(double) * 8));
+  if (pb->mode == PIE_MODE_BATCHED) PIE_CUDA(cudaMalloc(&c->d_acc, sizeof(float2) * HW));
+  PIE_CUDA(cudaMemsetAsync(c->d_inv_illum, 0, sizeof(float) * HW, st));
+  PIE_CUDA(cudaMemsetAsync(c->d_red, 0, sizeof(double) * 8, st));
+  k_illumination<<<grid_for((long long)N * n * n), kThreads, 0, st>>>(c->d_probe, c->d_pos, N, n, W, c->d_inv_illum);
+  k_max<<<grid_for(HW), kThreads, 0, st>>>(c->d_inv_illum, HW, (unsigned int*)c->d_red);
+  k_finish_illum<<<grid_for(HW), kThreads, 0, st>>>(c->d_inv_illum, HW, (const unsigned int*)c->d_red,
+                                                    (float)(pb->delta_rel > 0 ? pb->delta_rel : 1e-3), c->d_mask);
+  PIE_CUDA(cudaGetLastError());
+  PIE_CUDA(cudaStreamSynchronize(st));
+#undef PIE_TRY
+#undef PIE_CUDA
+  *out = c;
+  return PFT_OK;
+}
+
+int pie_ctx_colours(const pie_ctx* c, int* ncolours, int32_t* colour_of) {
+  if (!c || !ncolours) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  *ncolours = c->ncol;
+  if (colour_of)
+    for (int j = 0; j < c->npos; ++j) colour_of[j] = c->colour[j];
+  return PFT_OK;
+}
+
+int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stats* stats, void* stream) {
+  if (!c || !object) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
+  if (transform == PIE_TRANSFORM_FULL && c->full_kid < 0)
+    return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n in {16, 32, 64, 128}, not %d", c->n);
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long HW = (long long)c->H * c->W;
+  float2* obj = (float2*)object;
+  if (stats) PFT_CUDA_TRY(cudaMemcpyAsync(c->d_prev, obj, sizeof(float2) * HW, cudaMemcpyDeviceToDevice, st));
+  PFT_CUDA_TRY(cudaMemsetAsync(c->d_red, 0, sizeof(double) * 8, st));
+  const float n2 = (float)c->n * (float)c->n;
+  PieArgs a;
+  a.obj = obj;
+  a.objr = obj;
+  a.obj_w = c->W;
+  a.probe = c->d_probe;
+  a.pos = c->d_pos;
+  a.dat = transform == PIE_TRANSFORM_PFT ? c->d_ampc : c->d_amp;
+  a.gprobe = nullptr;
+  a.red = c->d_red;
+  if (c->pb.mode == PIE_MODE_COLOURED) {
+    a.coef = (float)(beta / ((double)c->probe_max2 * n2));
+    a.acc = nullptr;
+    for (int col = 0; col < c->ncol; ++col) {
+      a.list = c->d_sched + c->col_off[col];
+      a.count = c->col_off[col + 1] - c->col_off[col];
+      int rc = launch_pie(c, transform, MODE_COLOURED, a, st);
+      if (rc != PFT_OK) return rc;
+    }
+  } else {
+    PFT_CUDA_TRY(cudaMemsetAsync(c->d_acc, 0, sizeof(float2) * HW, st));
+    a.coef = 1.f / n2;
+    a.acc = c->d_acc;
+    a.list = nullptr;
+    a.count = c->npos;
+    int rc = launch_pie(c, transform, MODE_BATCHED, a, st);
+    if (rc != PFT_OK) return rc;
+    k_apply_batched<<<grid_for(HW), kThreads, 0, st>>>(obj, c->d_acc, c->d_inv_illum, (float)beta, HW);
+    PFT_CUDA_TRY(cudaGetLastError());
+  }
+  if (stats) {
+    k_diff_norms<<<grid_for(HW), kThreads, 0, st>>>(obj, c->d_prev, HW, c->d_red + 1);
+    PFT_CUDA_TRY(cudaGetLastError());
+    PFT_CUDA_TRY(cudaMemcpyAsync(c->h_red, c->d_red, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+    PFT_CUDA_TRY(cudaStreamSynchronize(st));
+    stats->phi = c->h_red[0] / ((double)c->npos * n2);
+    stats->rel_change = c->h_red[2] > 0 ? std::sqrt(c->h_red[1] / c->h_red[2]) : 0.0;
+    if (!std::isfinite(stats->phi) || !std::isfinite(stats->rel_change))
+      return pfth::set_error(PFT_ERR_NONFINITE, "non-finite objective or object change");
+  }
+  return PFT_OK;
+}
+
+int pie_nrmse(pie_ctx* c, const void* object, const void* truth, double* out, void* stream) {
+  if (!c || !object || !truth || !out) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long HW = (long long)c->H * c->W;
+  PFT_CUDA_TRY(cudaMemsetAsync(c->d_red + 3, 0, sizeof(double) * 4, st));
+  k_align_sums<<<grid_for(HW), kThreads, 0, st>>>((const float2*)object, (const float2*)truth, c->d_mask, HW,
+                                                  c->d_red + 3);
+  PFT_CUDA_TRY(cudaGetLastError());
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->h_red + 3, c->d_red + 3, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+  PFT_CUDA_TRY(cudaStreamSynchronize(st));
+  const double ip = std::hypot(c->h_red[3], c->h_red[4]);
+  const double e2 = std::max(0.0, c->h_red[5] + c->h_red[6] - 2.0 * ip);
+  *out = c->h_red[6] > 0 ? std::sqrt(e2 / c->h_red[6]) : 0.0;
+  if (!std::isfinite(*out)) return pfth::set_error(PFT_ERR_NONFINITE, "non-finite error norm");
+  return PFT_OK;
+}
+
+int warm_start_then_refine(pie_ctx* c, void* object, const pie_schedule* s, const void* truth, pie_trace* trace,
+                           int* ntrace, void* stream) {
+  if (!c || !object || !s) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (s->max_pft < 0 || s->max_full < 0) return pfth::set_error(PFT_ERR_INVALID_ARG, "negative sweep budget");
+  if (ntrace) *ntrace = 0;
+  const auto t0 = std::chrono::steady_clock::now();
+  int cnt = 0;
+  const struct { int tr; double beta, tol; int mx; } phases[2] = {
+      {PIE_TRANSFORM_PFT, s->beta_pft, s->tol_pft, s->max_pft},
+      {PIE_TRANSFORM_FULL, s->beta_full, s->tol_full, s->max_full}};
+  for (const auto& ph : phases) {
+    for (int it = 0; it < ph.mx; ++it) {
+      pie_stats stt;
+      int rc = pie_iteration(c, object, ph.tr, ph.beta, &stt, stream);
+      if (rc != PFT_OK) return rc;
+      double e = NAN;
+      if (truth) {
+        rc = pie_nrmse(c, object, truth, &e, stream);
+        if (rc != PFT_OK) return rc;
+      }
+      if (trace) {
+        trace[cnt].phase = ph.tr;
+        trace[cnt].phi = stt.phi;
+        trace[cnt].rel_change = stt.rel_change;
+        trace[cnt].nrmse = e;
+        trace[cnt].seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      }
+      ++cnt;
+      if (ntrace) *ntrace = cnt;
+      if (stt.rel_change < ph.tol) break;
+    }
+  }
+  return PFT_OK;
+}
+
+int pie_amp_loss_grad(pie_ctx* c, const void* object, const void* probe, void* grad_obj, void* grad_probe,
+                      double* loss, void* stream) {
+  if (!c || !object || !probe || !grad_obj || !loss) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long HW = (long long)c->H * c->W;
+  PFT_CUDA_TRY(cudaMemsetAsync(grad_obj, 0, sizeof(float2) * HW, st));
+  if (grad_probe) PFT_CUDA_TRY(cudaMemsetAsync(grad_probe, 0, sizeof(float2) * c->n * c->n, st));
+  PFT_CUDA_TRY(cudaMemsetAsync(c->d_red, 0, sizeof(double), st));
+  PieArgs a;
+  a.obj = nullptr;
+  a.objr = (const float2*)object;
+  a.obj_w = c->W;
+  a.probe = (const float2*)probe;
+  a.pos = c->d_pos;
+  a.list = nullptr;
+  a.count = c->npos;
+  a.dat = c->d_ampc;
+  a.coef = 1.f;
+  a.acc = (float2*)grad_obj;
+  a.gprobe = (float2*)grad_probe;
+  a.red = c->d_red;
+  int rc = launch_pie(c, PIE_TRANSFORM_PFT, MODE_GRAD, a, st);
+  if (rc != PFT_OK) return rc;
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->h_red, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFT_CUDA_TRY(cudaStreamSynchronize(st));
+  *loss = c->h_red[0];
+  if (!std::isfinite(*loss)) return pfth::set_error(PFT_ERR_NONFINITE, "non-finite loss");
+  return PFT_OK;
+}
+
+}  // extern "C"

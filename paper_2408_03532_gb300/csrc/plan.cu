@@ -1,0 +1,375 @@
+// PFT plans (Algorithm 4) and the batched forward / adjoint transforms
+// (Algorithm 5 and its exact adjoint) on sm_103a.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "coeffs.h"
+#include "plan.cuh"
+
+using namespace pftk;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// ------------------------------------------------------------ FP64 tables
+// Algorithm 1 / 4 tables for one axis, in FP64 with exact integer phase
+// reduction, rounded once to FP32:
+//   B[l][j]   = a_j (1 - 2 l / q)^j                    (real; w_j = i^j a_j)
+//   W'[j][t]  = i^j (t / p)^j e^{-i pi t / p},  t = t_idx - M/2
+//             = (t / p)^j e^{i pi m / p},  m = (j p / 2 - t) mod 2p
+//   tw[m]     = e^{-2 pi i m / p}
+__global__ void k_tables(int q, int p, int M, int r, const double* __restrict__ a, float* __restrict__ B,
+                         float2* __restrict__ W, float2* __restrict__ tw) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nB = q * RMAX, nW = RMAX * M;
+  if (tid < nB) {
+    const int l = tid / RMAX, j = tid % RMAX;
+    double v = 0.0;
+    if (j < r) v = a[j] * pow((double)(q - 2 * l) / (double)q, (double)j);
+    B[tid] = (float)v;
+  } else if (tid < nB + nW) {
+    const int i = tid - nB, j = i / M, ti = i % M;
+    const long long t = (long long)ti - M / 2;
+    float2 out = make_float2(0.f, 0.f);
+    if (j < r) {
+      const double mag = (j == 0) ? 1.0 : pow((double)t / (double)p, (double)j);
+      long long m = ((long long)j * (p / 2) - t) % (2LL * p);
+      if (m < 0) m += 2LL * p;
+      double s, c;
+      sincospi((double)m / (double)p, &s, &c);
+      out = make_float2((float)(mag * c), (float)(mag * s));
+    }
+    W[i] = out;
+  } else if (tid < nB + nW + p / 2) {
+    const int m = tid - nB - nW;
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)p, &s, &c);
+    tw[m] = make_float2((float)c, (float)s);
+  }
+}
+
+// --------------------------------------------------------- frame kernels
+template <int P, int Q, int MP>
+struct FrameShape {
+  static constexpr int N = P * Q, M = MP * P, G = 32 / P;
+  using L = YLayout<Q, M>;
+  static constexpr int OFF_W1 = 0;
+  static constexpr int OFF_W2 = OFF_W1 + RMAX * M;
+  static constexpr int OFF_TW = OFF_W2 + RMAX * M;
+  static constexpr int OFF_Y = OFF_TW + 16;
+  static constexpr int OFF_Z = OFF_Y + N * L::S;
+  static constexpr int ZS = M + 1;
+  static constexpr int FLOATS2 = OFF_Z + M * ZS;
+  static constexpr size_t SMEM = sizeof(float2) * FLOATS2;
+};
+
+template <int Q>
+__device__ __forceinline__ void load_block_v4(const float2* __restrict__ src, float2 (&x)[Q]) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int i = 0; i < Q / 2; ++i) {
+    float4 v = __ldg(s4 + i);
+    x[2 * i] = make_float2(v.x, v.y);
+    x[2 * i + 1] = make_float2(v.z, v.w);
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void store_block_v4(float2* dst, const float2 (&x)[Q]) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int i = 0; i < Q / 2; ++i) d4[i] = make_float4(x[2 * i].x, x[2 * i].y, x[2 * i + 1].x, x[2 * i + 1].y);
+}
+
+__device__ __forceinline__ void load_tables(float2* sm, const float2* __restrict__ gW, const float2* __restrict__ gtw,
+                                            int nW, int off_tw, int p) {
+  for (int i = threadIdx.x; i < nW; i += blockDim.x) sm[i] = gW[i];
+  for (int i = threadIdx.x; i < p / 2; i += blockDim.x) sm[off_tw + i] = gtw[i];
+}
+
+// y[f] = A1 x[f] A2^T  (Algorithm 5), one frame per CTA iteration.
+template <int P, int Q, int MP>
+__global__ void __launch_bounds__(kThreads) k_pft_fwd(const float2* __restrict__ x, float2* __restrict__ y,
+                                                      long long batch, const __grid_constant__ PftConst c,
+                                                      const float2* __restrict__ gW, const float2* __restrict__ gtw) {
+  using S = FrameShape<P, Q, MP>;
+  using T = Pft1D<P, Q, MP>;
+  constexpr int N = S::N, M = S::M, G = S::G;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* sW1 = sm + S::OFF_W1;
+  float2* sW2 = sm + S::OFF_W2;
+  float2* stw = sm + S::OFF_TW;
+  float2* sY = sm + S::OFF_Y;
+  float2* sZ = sm + S::OFF_Z;
+  load_tables(sm, gW, gtw, 2 * RMAX * M, S::OFF_TW, P);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = lane % P, g = lane / P;
+  for (long long f = blockIdx.x; f < batch; f += gridDim.x) {
+    const float2* xf = x + f * (long long)(N * N);
+    // rows: axis 2
+    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
+      const int u = u0 + g;
+      float2 xv[Q];
+      load_block_v4<Q>(xf + u * N + Q * k, xv);
+      T::forward(xv, k, c.bh[1], sW2, stw, [&](int t, float2 v) { sY[S::L::at(u, t)] = v; });
+    }
+    __syncthreads();
+    // columns: axis 1
+    for (int cs0 = warp * G; cs0 < M; cs0 += kWarps * G) {
+      const int t2 = col_of<P>(cs0 + g);
+      float2 xv[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) xv[l] = sY[S::L::at(Q * k + l, t2)];
+      T::forward(xv, k, c.bh[0], sW1, stw, [&](int t1, float2 v) { sZ[t1 * S::ZS + t2] = v; });
+    }
+    __syncthreads();
+    float2* yf = y + f * (long long)(M * M);
+    for (int i = threadIdx.x; i < M * M; i += kThreads) yf[i] = sZ[(i / M) * S::ZS + (i % M)];
+    __syncthreads();
+  }
+}
+
+// x[f] = A1^H y[f] conj(A2)  (exact adjoint of k_pft_fwd).
+template <int P, int Q, int MP>
+__global__ void __launch_bounds__(kThreads) k_pft_adj(const float2* __restrict__ y, float2* __restrict__ x,
+                                                      long long batch, const __grid_constant__ PftConst c,
+                                                      const float2* __restrict__ gW, const float2* __restrict__ gtw) {
+  using S = FrameShape<P, Q, MP>;
+  using T = Pft1D<P, Q, MP>;
+  constexpr int N = S::N, M = S::M, G = S::G;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* sW1 = sm + S::OFF_W1;
+  float2* sW2 = sm + S::OFF_W2;
+  float2* stw = sm + S::OFF_TW;
+  float2* sY = sm + S::OFF_Y;
+  float2* sZ = sm + S::OFF_Z;
+  load_tables(sm, gW, gtw, 2 * RMAX * M, S::OFF_TW, P);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = lane % P, g = lane / P;
+  for (long long f = blockIdx.x; f < batch; f += gridDim.x) {
+    const float2* yf = y + f * (long long)(M * M);
+    for (int i = threadIdx.x; i < M * M; i += kThreads) sZ[(i / M) * S::ZS + (i % M)] = __ldg(yf + i);
+    __syncthreads();
+    // columns: adjoint of axis 1
+    for (int cs0 = warp * G; cs0 < M; cs0 += kWarps * G) {
+      const int t2 = col_of<P>(cs0 + g);
+      float2 xv[Q];
+      T::adjoint([&](int t1) { return sZ[t1 * S::ZS + t2]; }, k, c.bh[0], sW1, stw, xv);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) sY[S::L::at(Q * k + l, t2)] = xv[l];
+    }
+    __syncthreads();
+    // rows: adjoint of axis 2
+    float2* xf = x + f * (long long)(N * N);
+    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
+      const int u = u0 + g;
+      float2 xv[Q];
+      T::adjoint([&](int t) { return sY[S::L::at(u, t)]; }, k, c.bh[1], sW2, stw, xv);
+      store_block_v4<Q>(xf + u * N + Q * k, xv);
+    }
+    __syncthreads();
+  }
+}
+
+template <int P, int Q, int MP>
+pfth::FrameKernels make_frame_kernels() {
+  return pfth::FrameKernels{P, Q, MP, (const void*)k_pft_fwd<P, Q, MP>, (const void*)k_pft_adj<P, Q, MP>,
+                            FrameShape<P, Q, MP>::SMEM};
+}
+
+// Shapes built: M = 2P (m~/p = 1, the paper's choice) for the frame sizes of
+// the workloads (n = 32 ... 256, M = 16 ... 64).
+const pfth::FrameKernels g_frame_kernels[] = {
+    make_frame_kernels<8, 4, 2>(),   // n = 32,  M = 16
+    make_frame_kernels<8, 8, 2>(),   // n = 64,  M = 16
+    make_frame_kernels<16, 4, 2>(),  // n = 64,  M = 32
+    make_frame_kernels<8, 16, 2>(),  // n = 128, M = 16
+    make_frame_kernels<16, 8, 2>(),  // n = 128, M = 32
+    make_frame_kernels<32, 4, 2>(),  // n = 128, M = 64
+    make_frame_kernels<16, 16, 2>(), // n = 256, M = 32
+    make_frame_kernels<32, 8, 2>(),  // n = 256, M = 64
+};
+
+}  // namespace
+
+namespace pfth {
+
+int frame_kernel_count() { return (int)(sizeof(g_frame_kernels) / sizeof(g_frame_kernels[0])); }
+const FrameKernels* frame_kernels(int id) { return &g_frame_kernels[id]; }
+int find_frame_kernels(int P, int Q, int MP) {
+  for (int i = 0; i < frame_kernel_count(); ++i)
+    if (g_frame_kernels[i].P == P && g_frame_kernels[i].Q == Q && g_frame_kernels[i].MP == MP) return i;
+  return -1;
+}
+
+int build_plan(pft_plan* p, int n, int M, int P, double eps, int r_force) {
+  if (n <= 0 || M <= 0 || M % 2 || M > n)
+    return set_error(PFT_ERR_INVALID_ARG, "need n > 0 and even 0 < M <= n (n=%d M=%d)", n, M);
+  if (P == 0) P = M / 2;
+  if (P < 2 || n % P)
+    return set_error(PFT_ERR_INVALID_ARG, "p=%d must divide n=%d and be >= 2", P, n);
+  const int Q = n / P;
+  if (Q < 2 || (Q & (Q - 1)) || (P & (P - 1)))
+    return set_error(PFT_ERR_UNSUPPORTED, "p=%d, q=%d: powers of two >= 2 are built", P, Q);
+  if (M % P) return set_error(PFT_ERR_UNSUPPORTED, "M=%d must be a multiple of p=%d", M, P);
+  int r = r_force;
+  if (r <= 0) {
+    r = pftc::choose_r(eps, (M / 2.0) / P);
+    if (r < 0) return set_error(PFT_ERR_INVALID_ARG, "no r reaches eps=%g at m~/p=%g", eps, (M / 2.0) / P);
+  }
+  if (r > RMAX)
+    return set_error(PFT_ERR_UNSUPPORTED, "r=%d > %d terms (eps=%g, m~/p=%g): use a larger p", r, RMAX, eps,
+                     (M / 2.0) / P);
+  const int kid = find_frame_kernels(P, Q, M / P);
+  if (kid < 0) return set_error(PFT_ERR_UNSUPPORTED, "no kernel built for n=%d M=%d p=%d", n, M, P);
+  double xi = 0.0, a[pftc::kMaxTerms] = {0};
+  if (!pftc::design(eps, r, &xi, a, nullptr))
+    return set_error(PFT_ERR_INVALID_ARG, "coefficient design failed (eps=%g r=%d)", eps, r);
+
+  p->n1 = p->n2 = n;
+  p->M1 = p->M2 = M;
+  p->p1 = p->p2 = P;
+  p->q1 = p->q2 = Q;
+  p->r1 = p->r2 = r;
+  p->xi1 = p->xi2 = xi;
+  p->eps = eps;
+  p->kid = kid;
+
+  double* d_a = nullptr;
+  float* d_B1 = nullptr;
+  PFT_CUDA_TRY(cudaMalloc(&d_a, sizeof(double) * pftc::kMaxTerms));
+  PFT_CUDA_TRY(cudaMalloc(&p->d_W, sizeof(float2) * 2 * RMAX * M));
+  PFT_CUDA_TRY(cudaMalloc(&p->d_twp, sizeof(float2) * 16));
+  PFT_CUDA_TRY(cudaMalloc(&p->d_B, sizeof(float) * 2 * Q * RMAX));
+  PFT_CUDA_TRY(cudaMemcpy(d_a, a, sizeof(double) * r, cudaMemcpyHostToDevice));
+  const int total = Q * RMAX + RMAX * M + P / 2;
+  // square plans: both axes share one table set; generate axis 0, copy to axis 1
+  k_tables<<<(total + 127) / 128, 128>>>(Q, P, M, r, d_a, p->d_B, p->d_W, p->d_twp);
+  PFT_CUDA_TRY(cudaGetLastError());
+  PFT_CUDA_TRY(cudaMemcpy(p->d_W + RMAX * M, p->d_W, sizeof(float2) * RMAX * M, cudaMemcpyDeviceToDevice));
+  d_B1 = p->d_B + Q * RMAX;
+  PFT_CUDA_TRY(cudaMemcpy(d_B1, p->d_B, sizeof(float) * Q * RMAX, cudaMemcpyDeviceToDevice));
+  std::vector<float> hB(Q * RMAX);
+  PFT_CUDA_TRY(cudaMemcpy(hB.data(), p->d_B, sizeof(float) * Q * RMAX, cudaMemcpyDeviceToHost));
+  PFT_CUDA_TRY(cudaFree(d_a));
+  std::memset(&p->cst, 0, sizeof(p->cst));
+  for (int ax = 0; ax < 2; ++ax)
+    for (int l = 0; l <= Q / 2; ++l)
+      for (int j = 0; j < RMAX; ++j) p->cst.bh[ax][l][j] = hB[l * RMAX + j];
+  return PFT_OK;
+}
+
+}  // namespace pfth
+
+// ------------------------------------------------------------------ C ABI
+namespace {
+
+int launch_frames(const pft_plan* plan, const void* in, void* out, int64_t batch, void* stream, bool adjoint) {
+  if (!plan || (!in && batch) || (!out && batch)) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (batch < 0) return pfth::set_error(PFT_ERR_INVALID_ARG, "batch < 0");
+  if (batch == 0) return PFT_OK;
+  const pfth::FrameKernels* fk = pfth::frame_kernels(plan->kid);
+  const void* fn = adjoint ? fk->adj : fk->fwd;
+  static bool attr_set[64][2] = {};
+  if (!attr_set[plan->kid][adjoint]) {
+    PFT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fk->smem));
+    attr_set[plan->kid][adjoint] = true;
+  }
+  int per_sm = 0;
+  PFT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, fk->smem));
+  if (per_sm < 1) return pfth::set_error(PFT_ERR_UNSUPPORTED, "frame kernel does not fit on an SM");
+  long long grid = (long long)per_sm * pfth::sm_count();
+  if (grid > batch) grid = batch;
+  const float2* a = (const float2*)in;
+  float2* b = (float2*)out;
+  long long nb = batch;
+  PftConst cst = plan->cst;
+  const float2* W = plan->d_W;
+  const float2* tw = plan->d_twp;
+  void* args[] = {(void*)&a, (void*)&b, (void*)&nb, (void*)&cst, (void*)&W, (void*)&tw};
+  PFT_CUDA_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kThreads), args, fk->smem, (cudaStream_t)stream));
+  return PFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pft_plan_create(pft_plan** out, int n1, int n2, int M1, int M2, int p1, int p2, double eps, int r1, int r2,
+                    int path, int precision) {
+  if (!out) return pfth::set_error(PFT_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  if (eps == 0.0) eps = 1e-7;
+  if (!(eps > 0.0 && eps < 1.0)) return pfth::set_error(PFT_ERR_INVALID_ARG, "need 0 < eps < 1");
+  if (path != PFT_PATH_AUTO && path != PFT_PATH_FACTORISED && path != PFT_PATH_DIRECT)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown path %d", path);
+  if (precision != PFT_PREC_FP32) return pfth::set_error(PFT_ERR_UNSUPPORTED, "precision %d not built", precision);
+  if (path == PFT_PATH_DIRECT) return pfth::set_error(PFT_ERR_UNSUPPORTED, "the direct path is not built");
+  if (n1 != n2 || M1 != M2 || p1 != p2 || r1 != r2)
+    return pfth::set_error(PFT_ERR_UNSUPPORTED, "square frames (n1 = n2, M1 = M2, p1 = p2) are built");
+  pft_plan* p = new (std::nothrow) pft_plan();
+  if (!p) return pfth::set_error(PFT_ERR_OOM, "host allocation failed");
+  int rc = pfth::build_plan(p, n1, M1, p1, eps, r1);
+  if (rc != PFT_OK) {
+    pft_plan_destroy(p);
+    return rc;
+  }
+  p->path = PFT_PATH_FACTORISED;
+  p->precision = precision;
+  *out = p;
+  return PFT_OK;
+}
+
+int pft_plan_destroy(pft_plan* p) {
+  if (!p) return PFT_OK;
+  cudaFree(p->d_W);
+  cudaFree(p->d_twp);
+  cudaFree(p->d_B);
+  delete p;
+  return PFT_OK;
+}
+
+int pft_plan_info_get(const pft_plan* p, pft_plan_info* info) {
+  if (!p || !info) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  info->n1 = p->n1; info->n2 = p->n2; info->M1 = p->M1; info->M2 = p->M2;
+  info->p1 = p->p1; info->p2 = p->p2; info->q1 = p->q1; info->q2 = p->q2;
+  info->r1 = p->r1; info->r2 = p->r2; info->xi1 = p->xi1; info->xi2 = p->xi2;
+  info->eps = p->eps; info->path = p->path; info->precision = p->precision;
+  return PFT_OK;
+}
+
+int pft_plan_tables(const pft_plan* p, int axis, float* B, float* W) {
+  if (!p || axis < 0 || axis > 1) return pfth::set_error(PFT_ERR_INVALID_ARG, "bad plan or axis");
+  const int q = axis ? p->q2 : p->q1, M = axis ? p->M2 : p->M1, r = axis ? p->r2 : p->r1;
+  if (B) {
+    std::vector<float> hB(q * RMAX);
+    PFT_CUDA_TRY(cudaMemcpy(hB.data(), p->d_B + axis * q * RMAX, sizeof(float) * q * RMAX, cudaMemcpyDeviceToHost));
+    for (int l = 0; l < q; ++l)
+      for (int j = 0; j < r; ++j) B[l * r + j] = hB[l * RMAX + j];
+  }
+  if (W) {
+    std::vector<float2> hW(RMAX * M);
+    PFT_CUDA_TRY(cudaMemcpy(hW.data(), p->d_W + axis * RMAX * M, sizeof(float2) * RMAX * M, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < M; ++t)
+      for (int j = 0; j < r; ++j) {
+        W[2 * (t * r + j)] = hW[j * M + t].x;
+        W[2 * (t * r + j) + 1] = hW[j * M + t].y;
+      }
+  }
+  return PFT_OK;
+}
+
+int pft_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void* stream) {
+  return launch_frames(plan, x, y, batch, stream, false);
+}
+
+int pft_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void* stream) {
+  return launch_frames(plan, y, x, batch, stream, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,33 @@
+// Internal plan object shared by the transform and PIE translation units.
+#pragma once
+
+#include "pft_core.cuh"
+
+struct pft_plan {
+  int n1, n2, M1, M2, p1, p2, q1, q2, r1, r2;
+  double xi1, xi2, eps;
+  int path, precision;
+  pftk::PftConst cst;     // B rows for both axes (kernel parameter space)
+  float2* d_W = nullptr;  // [2][RMAX][M] : W'[axis][j][t_idx] (FP32 from FP64)
+  float2* d_twp = nullptr;  // [16] : e^{-2 pi i m / p}, m < p/2
+  float* d_B = nullptr;     // [2][q][RMAX] full B table (inspection only)
+  int kid = -1;             // index in the frame-kernel registry
+};
+
+namespace pfth {
+
+// Frame kernels built for one (P, Q, M/P) shape.
+struct FrameKernels {
+  int P, Q, MP;
+  const void* fwd;
+  const void* adj;
+  size_t smem;
+};
+int frame_kernel_count();
+const FrameKernels* frame_kernels(int id);
+int find_frame_kernels(int P, int Q, int MP);
+
+// Builds a square plan's tables; used by pft_plan_create and the PIE context.
+int build_plan(pft_plan* p, int n, int M, int P, double eps, int r_force);
+
+}  // namespace pfth

@@ -1,0 +1,319 @@
+"""Thin Python binding over the C ABI in include/pft.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``lib/libpft_gb300.so``; this module
+only passes device pointers, sizes and the current CUDA stream. It raises if
+the library has not been built (``python -m paper_2408_03532_gb300.build`` or
+``__graft_entry__.build()``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libpft_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pft.h")
+
+PFT_OK = 0
+PATH_AUTO, PATH_FACTORISED, PATH_DIRECT = 0, 1, 2
+PREC_FP32 = 0
+TRANSFORM_PFT, TRANSFORM_FULL = 0, 1
+MODE_COLOURED, MODE_BATCHED = 0, 1
+_ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "OOM"}
+
+
+class PftError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"PFT_ERR_{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in ("n1", "n2", "M1", "M2", "p1", "p2", "q1", "q2", "r1", "r2")] + [
+        ("xi1", ctypes.c_double), ("xi2", ctypes.c_double), ("eps", ctypes.c_double),
+        ("path", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class PieProblem(ctypes.Structure):
+    _fields_ = [("obj_h", ctypes.c_int), ("obj_w", ctypes.c_int), ("n", ctypes.c_int), ("npos", ctypes.c_int),
+                ("M", ctypes.c_int), ("p", ctypes.c_int), ("eps", ctypes.c_double), ("mode", ctypes.c_int),
+                ("path", ctypes.c_int), ("delta_rel", ctypes.c_double)]
+
+
+class PieStats(ctypes.Structure):
+    _fields_ = [("phi", ctypes.c_double), ("rel_change", ctypes.c_double)]
+
+
+class PieSchedule(ctypes.Structure):
+    _fields_ = [("beta_pft", ctypes.c_double), ("beta_full", ctypes.c_double), ("tol_pft", ctypes.c_double),
+                ("tol_full", ctypes.c_double), ("max_pft", ctypes.c_int), ("max_full", ctypes.c_int)]
+
+
+class PieTrace(ctypes.Structure):
+    _fields_ = [("phase", ctypes.c_int), ("phi", ctypes.c_double), ("rel_change", ctypes.c_double),
+                ("nrmse", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/pft.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\**(\w+)\s*\(", txt, flags=re.M)))
+
+
+def load() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "pft_last_error": (ctypes.c_char_p, []),
+        "pft_version": (ctypes.c_int, []),
+        "pft_design_coefficients": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, _P, _P, _P]),
+        "pft_choose_r": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _P]),
+        "pft_plan_create": (ctypes.c_int, [_P] + [ctypes.c_int] * 6 + [ctypes.c_double] + [ctypes.c_int] * 4),
+        "pft_plan_destroy": (ctypes.c_int, [_P]),
+        "pft_plan_info_get": (ctypes.c_int, [_P, _P]),
+        "pft_plan_tables": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+        "pft_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
+        "pft_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
+        "pft_fft2": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_int, _P]),
+        "pft_fft_crop": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P]),
+        "pie_ctx_create": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+        "pie_ctx_destroy": (ctypes.c_int, [_P]),
+        "pie_ctx_colours": (ctypes.c_int, [_P, _P, _P]),
+        "pie_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
+        "warm_start_then_refine": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+        "pie_nrmse": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+        "pie_amp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int) -> None:
+    if rc != PFT_OK:
+        raise PftError(rc, load().pft_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else t.data_ptr()
+
+
+def _need(t, dtype, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape[-len(shape):]) != tuple(shape):
+        raise ValueError(f"{name}: trailing shape {tuple(t.shape)} != {shape}")
+
+
+# ------------------------------------------------------------ offline phase
+def design_coefficients(eps: float, r: int) -> tuple[float, np.ndarray, float]:
+    """(xi(eps, r), a (w_j = i^j a_j), uniform error) from the host designer."""
+    lib = load()
+    xi, err = ctypes.c_double(), ctypes.c_double()
+    a = np.zeros(r, dtype=np.float64)
+    _check(lib.pft_design_coefficients(eps, r, ctypes.byref(xi), a.ctypes.data, ctypes.byref(err)))
+    return xi.value, a, err.value
+
+
+def choose_r(eps: float, ratio: float) -> int:
+    r = ctypes.c_int()
+    _check(load().pft_choose_r(eps, ratio, ctypes.byref(r)))
+    return r.value
+
+
+# ------------------------------------------------------------------- plans
+class Plan:
+    """A square PFT plan (Algorithm 4): n x n frames -> centred M x M outputs."""
+
+    def __init__(self, n: int, M: int, p: int = 0, eps: float = 1e-7, r: int = 0,
+                 path: int = PATH_AUTO, precision: int = PREC_FP32):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.pft_plan_create(ctypes.byref(h), n, n, M, M, p, p, eps, r, r, path, precision))
+        self._h = h
+        info = PlanInfo()
+        _check(lib.pft_plan_info_get(h, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+        self.n, self.M = n, M
+
+    def tables(self, axis: int = 0) -> tuple[np.ndarray, np.ndarray]:
+        q, r, M = self.info["q1"], self.info["r1"], self.M
+        B = np.zeros((q, r), dtype=np.float32)
+        W = np.zeros((M, r), dtype=np.complex64)
+        _check(load().pft_plan_tables(self._h, axis, B.ctypes.data, W.ctypes.data))
+        return B, W
+
+    def forward(self, x, out=None, stream=None):
+        import torch
+        _need(x, torch.complex64, (self.n, self.n), "x")
+        lead = x.shape[:-2]
+        if out is None:
+            out = torch.empty(*lead, self.M, self.M, dtype=torch.complex64, device=x.device)
+        batch = int(np.prod(lead)) if len(lead) else 1
+        _check(load().pft_forward(self._h, _ptr(x), _ptr(out), batch, _stream(stream)))
+        return out
+
+    def adjoint(self, y, out=None, stream=None):
+        import torch
+        _need(y, torch.complex64, (self.M, self.M), "y")
+        lead = y.shape[:-2]
+        if out is None:
+            out = torch.empty(*lead, self.n, self.n, dtype=torch.complex64, device=y.device)
+        batch = int(np.prod(lead)) if len(lead) else 1
+        _check(load().pft_adjoint(self._h, _ptr(y), _ptr(out), batch, _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pft_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fft2(x, inverse: bool = False, out=None, stream=None):
+    """Unnormalised full 2-D DFT of n x n frames (inverse: its conjugate transpose)."""
+    import torch
+    _need(x, torch.complex64, None, "x")
+    n = x.shape[-1]
+    out = torch.empty_like(x) if out is None else out
+    batch = int(np.prod(x.shape[:-2])) if x.dim() > 2 else 1
+    _check(load().pft_fft2(_ptr(x), _ptr(out), n, batch, int(inverse), _stream(stream)))
+    return out
+
+
+def fft_crop(x, M: int, out=None, stream=None):
+    """Full 2-D FFT then the centred M x M crop (baseline)."""
+    import torch
+    _need(x, torch.complex64, None, "x")
+    n = x.shape[-1]
+    lead = x.shape[:-2]
+    if out is None:
+        out = torch.empty(*lead, M, M, dtype=torch.complex64, device=x.device)
+    batch = int(np.prod(lead)) if len(lead) else 1
+    _check(load().pft_fft_crop(_ptr(x), _ptr(out), n, M, batch, _stream(stream)))
+    return out
+
+
+# --------------------------------------------------------------------- PIE
+@dataclass
+class Schedule:
+    beta_pft: float = 1.0
+    beta_full: float = 1.0
+    tol_pft: float = 1e-2
+    tol_full: float = 5e-4
+    max_pft: int = 50
+    max_full: int = 100
+
+
+class PieContext:
+    """One ptychography problem resident on the GPU (probe, scan, amplitudes, plans)."""
+
+    def __init__(self, obj_shape, probe, positions, intensities, M: int, p: int = 0, eps: float = 1e-7,
+                 mode: int = MODE_COLOURED, delta_rel: float = 1e-3, stream=None):
+        import torch
+        n = probe.shape[-1]
+        _need(probe, torch.complex64, (n, n), "probe")
+        _need(intensities, torch.float32, (n, n), "intensities")
+        pos = np.ascontiguousarray(np.asarray(positions, dtype=np.int32).reshape(-1, 2))
+        prob = PieProblem(int(obj_shape[0]), int(obj_shape[1]), n, len(pos), M, p, eps, mode, PATH_AUTO, delta_rel)
+        h = ctypes.c_void_p()
+        _check(load().pie_ctx_create(ctypes.byref(h), ctypes.byref(prob), _ptr(probe), pos.ctypes.data,
+                                     _ptr(intensities), _stream(stream)))
+        self._h = h
+        self.shape = (int(obj_shape[0]), int(obj_shape[1]))
+        self.n, self.M, self.npos = n, M, len(pos)
+
+    def colours(self) -> np.ndarray:
+        nc = ctypes.c_int()
+        col = np.zeros(self.npos, dtype=np.int32)
+        _check(load().pie_ctx_colours(self._h, ctypes.byref(nc), col.ctypes.data))
+        return col
+
+    def _obj(self, obj, name="object"):
+        import torch
+        _need(obj, torch.complex64, self.shape, name)
+
+    def iteration(self, obj, transform: int = TRANSFORM_PFT, beta: float = 1.0, stats: bool = True, stream=None):
+        self._obj(obj)
+        st = PieStats()
+        _check(load().pie_iteration(self._h, _ptr(obj), transform, beta,
+                                    ctypes.byref(st) if stats else None, _stream(stream)))
+        return {"phi": st.phi, "rel_change": st.rel_change} if stats else None
+
+    def nrmse(self, obj, truth, stream=None) -> float:
+        self._obj(obj)
+        self._obj(truth, "truth")
+        out = ctypes.c_double()
+        _check(load().pie_nrmse(self._h, _ptr(obj), _ptr(truth), ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def warm_start_then_refine(self, obj, schedule: Schedule, truth=None, stream=None) -> list[dict]:
+        self._obj(obj)
+        if truth is not None:
+            self._obj(truth, "truth")
+        s = PieSchedule(schedule.beta_pft, schedule.beta_full, schedule.tol_pft, schedule.tol_full,
+                        schedule.max_pft, schedule.max_full)
+        cap = max(1, schedule.max_pft + schedule.max_full)
+        tr = (PieTrace * cap)()
+        cnt = ctypes.c_int()
+        _check(load().warm_start_then_refine(self._h, _ptr(obj), ctypes.byref(s), _ptr(truth), tr,
+                                             ctypes.byref(cnt), _stream(stream)))
+        return [{"phase": "pft" if t.phase == TRANSFORM_PFT else "full", "phi": t.phi,
+                 "rel_change": t.rel_change, "nrmse": t.nrmse, "seconds": t.seconds} for t in tr[:cnt.value]]
+
+    def amp_loss_grad(self, obj, probe, need_probe_grad: bool = True, stream=None):
+        import torch
+        self._obj(obj)
+        _need(probe, torch.complex64, (self.n, self.n), "probe")
+        g_obj = torch.empty_like(obj)
+        g_probe = torch.empty_like(probe) if need_probe_grad else None
+        loss = ctypes.c_double()
+        _check(load().pie_amp_loss_grad(self._h, _ptr(obj), _ptr(probe), _ptr(g_obj), _ptr(g_probe),
+                                        ctypes.byref(loss), _stream(stream)))
+        return loss.value, g_obj, g_probe
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pie_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

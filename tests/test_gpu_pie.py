@@ -1,0 +1,177 @@
+"""GPU parity of PIE sweeps, the hybrid driver, the error metric and the
+amplitude-loss gradient against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import coeffs, grad as ograd, pie as opie
+from paper_2408_03532_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_2408_03532_gb300 import build as libbuild
+    from paper_2408_03532_gb300 import pft
+    libbuild.build()
+    pft.load()
+    return torch, pft
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def c64(a, torch):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).cuda()
+
+
+def make_ctx(P, torch, pft, mode=0):
+    return pft.PieContext(P["obj"].shape, c64(P["probe"], torch), P["pos"],
+                          torch.from_numpy(P["intensities"].astype(np.float32)).cuda(), M=P["M"], mode=mode)
+
+
+def oracle_T(P, transform):
+    n = P["probe"].shape[0]
+    if transform == "full":
+        return opie.full_transform(n, n), opie.amplitudes(P["intensities"])
+    M = P["M"]
+    P1, P2 = coeffs.plan_2d(n, n, M, M, M // 2, M // 2)
+    return opie.pft_transform(P1, P2), opie.amplitudes(P["intensities"], M)
+
+
+@pytest.fixture(scope="module")
+def small():
+    return synth.small_raster_problem()
+
+
+@pytest.fixture(scope="module")
+def mid():
+    """n = 128, M = 32 on a 384^2 object with 100 Fermat positions (Poisson)."""
+    return synth.spiral_problem(side=384, n=128, count=100, peak_photons=1e4, M=32)
+
+
+def test_colouring_matches_oracle(env, small, mid):
+    torch, pft = env
+    for P in (small, mid):
+        ctx = make_ctx(P, torch, pft)
+        n = P["probe"].shape[0]
+        assert np.array_equal(ctx.colours(), opie.greedy_colouring(P["pos"], n, n))
+
+
+@pytest.mark.parametrize("transform", ["pft", "full"])
+@pytest.mark.parametrize("which", ["small", "mid"])
+def test_coloured_sweep_matches_oracle(env, small, mid, transform, which):
+    """One sweep of sequential PIE in colour-major order."""
+    torch, pft = env
+    P = small if which == "small" else mid
+    ctx = make_ctx(P, torch, pft)
+    z = c64(P["init"], torch)
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    st = ctx.iteration(z, tr, 0.9)
+    T, d = oracle_T(P, transform)
+    n = P["probe"].shape[0]
+    order = opie.colour_major_order(opie.greedy_colouring(P["pos"], n, n))
+    zo, phi = opie.pie_sweep(P["init"], P["probe"], P["pos"], d, T, 0.9, order)
+    assert rel(z.cpu().numpy(), zo) < TOL
+    assert st["phi"] == pytest.approx(phi, rel=TOL)
+    assert st["rel_change"] == pytest.approx(opie.relative_change(zo, P["init"]), rel=1e-4)
+
+
+@pytest.mark.parametrize("transform", ["pft", "full"])
+def test_batched_sweep_matches_oracle(env, small, transform):
+    torch, pft = env
+    P = small
+    ctx = make_ctx(P, torch, pft, mode=pft.MODE_BATCHED)
+    z = c64(P["init"], torch)
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    st = ctx.iteration(z, tr, 1.0)
+    T, d = oracle_T(P, transform)
+    zo, phi = opie.batched_sweep(P["init"], P["probe"], P["pos"], d, T, 1.0, delta_rel=1e-3)
+    assert rel(z.cpu().numpy(), zo) < TOL
+    assert st["phi"] == pytest.approx(phi, rel=TOL)
+
+
+def test_hybrid_trajectory_matches_oracle(env, small):
+    """Algorithm 3 with 10 PFT and 10 full sweeps: the per-sweep error of the GPU
+    run stays within 1e-4 of the oracle's in the same (colour-major) order."""
+    torch, pft = env
+    P = small
+    ctx = make_ctx(P, torch, pft)
+    z = c64(P["init"], torch)
+    truth = c64(P["obj"], torch)
+    tr = ctx.warm_start_then_refine(z, pft.Schedule(1.0, 1.0, 0.0, 0.0, 10, 10), truth)
+    assert [t["phase"] for t in tr] == ["pft"] * 10 + ["full"] * 10
+    T, _ = oracle_T(P, "pft")
+    order = opie.colour_major_order(opie.greedy_colouring(P["pos"], 32, 32))
+    zo, tro = opie.hybrid_pie(P["init"], P["probe"], P["pos"], P["intensities"], T, P["M"], 1.0, 1.0,
+                              0.0, 10, 0.0, 10, order=order, truth=P["obj"])
+    for g, o in zip(tr, tro):
+        assert abs(g["nrmse"] - o["nrmse"]) < 1e-4
+        assert g["phi"] == pytest.approx(o["phi"], rel=1e-3)
+    assert rel(z.cpu().numpy(), zo) < 1e-4
+    assert all(t["seconds"] >= 0 for t in tr)
+
+
+def test_nrmse_matches_oracle(env, small):
+    torch, pft = env
+    P = small
+    ctx = make_ctx(P, torch, pft)
+    z = P["init"] * np.exp(0.3j)
+    got = ctx.nrmse(c64(z, torch), c64(P["obj"], torch))
+    mask = opie.illuminated_mask(P["probe"], P["pos"], P["obj"].shape)
+    ref = opie.nrmse(z.astype(np.complex64).astype(np.complex128), P["obj"].astype(np.complex64), mask)
+    assert got == pytest.approx(ref, rel=1e-5)
+    # global phase is removed: the truth rotated has zero error
+    assert ctx.nrmse(c64(P["obj"] * np.exp(1.1j), torch), c64(P["obj"], torch)) < 1e-6
+
+
+def test_gradient_matches_oracle(env):
+    """Amplitude loss through the PFT on the 512^2 / 64^2 / 400-position problem."""
+    torch, pft = env
+    G = synth.gradient_problem()
+    ctx = make_ctx(G, torch, pft)
+    loss, gz, gw = ctx.amp_loss_grad(c64(G["init"], torch), c64(G["probe"], torch))
+    P1, P2 = coeffs.plan_2d(64, 64, 32, 32, 16, 16)
+    T = opie.pft_transform(P1, P2)
+    d = opie.amplitudes(G["intensities"], 32)
+    lo, gzo, gwo = ograd.amplitude_loss_grad(G["init"].astype(np.complex64).astype(np.complex128),
+                                             G["probe"].astype(np.complex64).astype(np.complex128),
+                                             G["pos"], d.astype(np.float32).astype(np.float64), T)
+    assert loss == pytest.approx(lo, rel=TOL)
+    assert rel(gz.cpu().numpy(), gzo) < TOL
+    assert rel(gw.cpu().numpy(), gwo) < TOL
+
+
+def test_full_size_sweeps_match_oracle(env):
+    """The 1024^2 / 128^2 / 3600-position Fermat problem at full size, in the
+    launch configuration the benchmark times: one PFT and one full sweep."""
+    torch, pft = env
+    P = synth.spiral_problem()
+    ctx = make_ctx(P, torch, pft)
+    order = opie.colour_major_order(ctx.colours().astype(np.int64))
+    assert np.array_equal(ctx.colours(), opie.greedy_colouring(P["pos"], 128, 128))
+    for transform in ("pft", "full"):
+        z = c64(P["init"], torch)
+        ctx.iteration(z, pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL, 1.0)
+        T, d = oracle_T(P, transform)
+        zo, _ = opie.pie_sweep(P["init"], P["probe"], P["pos"], d, T, 1.0, order)
+        assert rel(z.cpu().numpy(), zo) < TOL
+
+
+def test_errors(env, small):
+    torch, pft = env
+    P = small
+    bad = P["pos"].copy()
+    bad[3] = (200, 0)
+    with pytest.raises(pft.PftError) as e:
+        pft.PieContext(P["obj"].shape, c64(P["probe"], torch), bad,
+                       torch.from_numpy(P["intensities"].astype(np.float32)).cuda(), M=16)
+    assert e.value.code == -1
+    with pytest.raises(pft.PftError):
+        pft.PieContext(P["obj"].shape, c64(P["probe"], torch), P["pos"],
+                       torch.from_numpy(P["intensities"].astype(np.float32)).cuda(), M=15)
