@@ -15,7 +15,7 @@
 #include <new>
 #include <vector>
 
-#include "fft_core.cuh"
+#include "pie_kernels.cuh"
 #include "plan.cuh"
 
 using namespace pftk;
@@ -24,236 +24,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-
-enum { MODE_COLOURED = 0, MODE_BATCHED = 1, MODE_GRAD = 2 };
-
-struct PieArgs {
-  float2* obj;              // object [H][W] (read; written in MODE_COLOURED)
-  const float2* objr;       // object read pointer (= obj, or the gradient's input)
-  long long obj_w;
-  const float2* probe;      // [n][n]
-  const int2* pos;          // [N] top-left (row, col)
-  const int* list;          // positions to process (nullptr = 0..count-1)
-  int count;
-  const float* dat;         // amplitudes: [N][M][M] centred crop, or [N][n][n] FFT order
-  float coef;               // update scale
-  float2* acc;              // MODE_BATCHED: sum conj(w) dpsi; MODE_GRAD: grad_obj
-  float2* gprobe;           // MODE_GRAD: grad_probe (may be null)
-  double* red;              // red[0] += sum ||R||^2 (MODE_GRAD: loss)
-};
-
-// Modulus-projection residual (Eq. 3) and its contribution to the objective.
-template <int MODE>
-__device__ __forceinline__ float2 residual(float2 Psi, float d, double& acc) {
-  const float m2 = cabs2(Psi);
-  if (MODE == MODE_GRAD) {
-    // sgn(0) = 0; gradient of sum (|Psi| - d)^2 is 2 R
-    if (m2 > 0.f) {
-      const float m = sqrtf(m2);
-      const float diff = m - d;
-      acc += (double)diff * (double)diff;
-      return cscale(Psi, 2.f * diff / m);
-    }
-    acc += (double)d * (double)d;
-    return make_float2(0.f, 0.f);
-  }
-  // theta(0) = 0: a zero coefficient is replaced by d
-  float2 R;
-  if (m2 > 0.f) {
-    const float m = sqrtf(m2);
-    R = cscale(Psi, 1.f - d / m);
-  } else {
-    R = make_float2(-d, 0.f);
-  }
-  acc += (double)cabs2(R);
-  return R;
-}
-
-template <int MODE>
-__device__ __forceinline__ void apply_update(const PieArgs& a, long long oidx, float2 w, float2 dpsi, int pidx) {
-  if (MODE == MODE_COLOURED) {
-    float2 o = a.obj[oidx];
-    const float2 u = cmulc(dpsi, w);  // conj(w) dpsi
-    o.x = fmaf(-a.coef, u.x, o.x);
-    o.y = fmaf(-a.coef, u.y, o.y);
-    a.obj[oidx] = o;
-  } else if (MODE == MODE_BATCHED) {
-    atomicAdd(a.acc + oidx, cscale(cmulc(dpsi, w), a.coef));
-  } else {
-    atomicAdd(a.acc + oidx, cmulc(dpsi, w));
-    if (a.gprobe) atomicAdd(a.gprobe + pidx, cmulc(dpsi, a.objr[oidx]));
-  }
-}
-
-__device__ __forceinline__ void block_accumulate(double v, double* red_smem, double* out) {
-  double s = block_sum(v, red_smem);
-  if (threadIdx.x == 0 && s != 0.0) atomicAdd(out, s);
-}
-
-// ------------------------------------------------------ PFT position kernel
-template <int P, int Q, int MP>
-struct PieShape {
-  static constexpr int N = P * Q, M = MP * P, G = 32 / P;
-  using L = YLayout<Q, M>;
-  static constexpr int OFF_W1 = 0;
-  static constexpr int OFF_W2 = OFF_W1 + RMAX * M;
-  static constexpr int OFF_TW = OFF_W2 + RMAX * M;
-  static constexpr int OFF_Y = OFF_TW + 16;
-  static constexpr int ZS = M + 1;
-  static constexpr int OFF_Z = OFF_Y + N * L::S;
-  static constexpr int OFF_RED = OFF_Z + M * ZS;
-  static constexpr size_t SMEM = sizeof(float2) * (OFF_RED + kWarps);
-};
-
-template <int P, int Q, int MP, int MODE>
-__global__ void __launch_bounds__(kThreads) k_pie_pft(PieArgs a, const __grid_constant__ PftConst c,
-                                                      const float2* __restrict__ gW,
-                                                      const float2* __restrict__ gtw) {
-  using S = PieShape<P, Q, MP>;
-  using T = Pft1D<P, Q, MP>;
-  constexpr int N = S::N, M = S::M, G = S::G;
-  extern __shared__ __align__(16) float2 sm[];
-  float2* sW1 = sm + S::OFF_W1;
-  float2* sW2 = sm + S::OFF_W2;
-  float2* stw = sm + S::OFF_TW;
-  float2* sY = sm + S::OFF_Y;
-  float2* sZ = sm + S::OFF_Z;
-  double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
-  for (int i = threadIdx.x; i < 2 * RMAX * M; i += kThreads) sm[i] = gW[i];
-  for (int i = threadIdx.x; i < P / 2; i += kThreads) stw[i] = gtw[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int k = lane % P, g = lane / P;
-  for (int it = blockIdx.x; it < a.count; it += gridDim.x) {
-    const int j = a.list ? a.list[it] : it;
-    const int2 rc = a.pos[j];
-    const long long obase = (long long)rc.x * a.obj_w + rc.y;
-    // rows: exit wave and axis-2 transform
-    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
-      const int u = u0 + g;
-      float2 xv[Q];
-#pragma unroll
-      for (int l = 0; l < Q; ++l) {
-        const int v = Q * k + l;
-        xv[l] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
-      }
-      T::forward(xv, k, c.bh[1], sW2, stw, [&](int t, float2 val) { sY[S::L::at(u, t)] = val; });
-    }
-    __syncthreads();
-    for (int cs0 = warp * G; cs0 < M; cs0 += kWarps * G) {
-      const int t2 = col_of<P>(cs0 + g);
-      float2 xv[Q];
-#pragma unroll
-      for (int l = 0; l < Q; ++l) xv[l] = sY[S::L::at(Q * k + l, t2)];
-      T::forward(xv, k, c.bh[0], sW1, stw, [&](int t1, float2 val) { sZ[t1 * S::ZS + t2] = val; });
-    }
-    __syncthreads();
-    // modulus projection on the M x M coefficients
-    const float* dj = a.dat + (long long)j * (M * M);
-    double part = 0.0;
-    for (int i = threadIdx.x; i < M * M; i += kThreads) {
-      float2* z = sZ + (i / M) * S::ZS + (i % M);
-      *z = residual<MODE>(*z, __ldg(dj + i), part);
-    }
-    block_accumulate(part, sred, a.red);
-    __syncthreads();
-    // adjoint: columns then rows
-    for (int cs0 = warp * G; cs0 < M; cs0 += kWarps * G) {
-      const int t2 = col_of<P>(cs0 + g);
-      float2 xv[Q];
-      T::adjoint([&](int t1) { return sZ[t1 * S::ZS + t2]; }, k, c.bh[0], sW1, stw, xv);
-#pragma unroll
-      for (int l = 0; l < Q; ++l) sY[S::L::at(Q * k + l, t2)] = xv[l];
-    }
-    __syncthreads();
-    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
-      const int u = u0 + g;
-      float2 xv[Q];
-      T::adjoint([&](int t) { return sY[S::L::at(u, t)]; }, k, c.bh[1], sW2, stw, xv);
-#pragma unroll
-      for (int l = 0; l < Q; ++l) {
-        const int v = Q * k + l;
-        apply_update<MODE>(a, obase + (long long)u * a.obj_w + v, __ldg(a.probe + u * N + v), xv[l], u * N + v);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// ----------------------------------------------------- full-FFT position kernel
-template <int N, int MODE>
-__global__ void __launch_bounds__(kThreads) k_pie_full(PieArgs a, const float2* __restrict__ gtw) {
-  using F = Fft<N>;
-  constexpr int L = F::L, E = F::E, G = F::G, S = F::S;
-  extern __shared__ __align__(16) float2 sm[];
-  float2* tw = sm;
-  float2* sF = sm + N;
-  double* sred = reinterpret_cast<double*>(sF + N * S);
-  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = gtw[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int l = lane % L, g = lane / L;
-  for (int it = blockIdx.x; it < a.count; it += gridDim.x) {
-    const int j = a.list ? a.list[it] : it;
-    const int2 rc = a.pos[j];
-    const long long obase = (long long)rc.x * a.obj_w + rc.y;
-    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
-      const int u = u0 + g;
-      float2 x[E];
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int v = l + L * e;
-        x[e] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
-      }
-      F::fwd(x, l, tw);
-#pragma unroll
-      for (int p = 0; p < E; ++p) sF[u * S + p * L + l] = x[p];
-    }
-    __syncthreads();
-    for (int b0 = warp * G; b0 < N; b0 += kWarps * G) {
-      const int b = b0 + g;
-      float2 x[E];
-#pragma unroll
-      for (int e = 0; e < E; ++e) x[e] = sF[(l + L * e) * S + b];
-      F::fwd(x, l, tw);
-#pragma unroll
-      for (int p = 0; p < E; ++p) sF[(p * L + l) * S + b] = x[p];
-    }
-    __syncthreads();
-    const float* dj = a.dat + (long long)j * (N * N);
-    double part = 0.0;
-    for (int i = threadIdx.x; i < N * N; i += kThreads) {
-      const int sa = i / N, sb = i % N;
-      float2* z = sF + sa * S + sb;
-      *z = residual<MODE>(*z, __ldg(dj + F::freq_of_slot(sa) * N + F::freq_of_slot(sb)), part);
-    }
-    block_accumulate(part, sred, a.red);
-    __syncthreads();
-    for (int b0 = warp * G; b0 < N; b0 += kWarps * G) {
-      const int b = b0 + g;
-      float2 x[E];
-#pragma unroll
-      for (int p = 0; p < E; ++p) x[p] = sF[(p * L + l) * S + b];
-      F::adj(x, l, tw);
-#pragma unroll
-      for (int e = 0; e < E; ++e) sF[(l + L * e) * S + b] = x[e];
-    }
-    __syncthreads();
-    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
-      const int u = u0 + g;
-      float2 x[E];
-#pragma unroll
-      for (int p = 0; p < E; ++p) x[p] = sF[u * S + p * L + l];
-      F::adj(x, l, tw);
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int v = l + L * e;
-        apply_update<MODE>(a, obase + (long long)u * a.obj_w + v, __ldg(a.probe + u * N + v), x[e], u * N + v);
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // ------------------------------------------------------------ helper kernels
 __global__ void k_amplitudes(const float* __restrict__ I, float* __restrict__ d, float* __restrict__ dc,
@@ -348,43 +118,6 @@ __global__ void k_apply_batched(float2* __restrict__ z, const float2* __restrict
   }
 }
 
-// -------------------------------------------------------------- registries
-struct PftPieKernels {
-  int P, Q, MP;
-  const void* k[3];
-  size_t smem;
-};
-
-template <int P, int Q, int MP>
-PftPieKernels make_pft_pie() {
-  return PftPieKernels{P, Q, MP,
-                       {(const void*)k_pie_pft<P, Q, MP, MODE_COLOURED>, (const void*)k_pie_pft<P, Q, MP, MODE_BATCHED>,
-                        (const void*)k_pie_pft<P, Q, MP, MODE_GRAD>},
-                       PieShape<P, Q, MP>::SMEM};
-}
-
-const PftPieKernels g_pft_pie[] = {
-    make_pft_pie<8, 4, 2>(),  make_pft_pie<8, 8, 2>(),  make_pft_pie<16, 4, 2>(), make_pft_pie<8, 16, 2>(),
-    make_pft_pie<16, 8, 2>(), make_pft_pie<32, 4, 2>(), make_pft_pie<16, 16, 2>(), make_pft_pie<32, 8, 2>(),
-};
-
-struct FullPieKernels {
-  int N;
-  const void* k[3];
-  size_t smem;
-};
-
-template <int N>
-FullPieKernels make_full_pie() {
-  return FullPieKernels{N,
-                        {(const void*)k_pie_full<N, MODE_COLOURED>, (const void*)k_pie_full<N, MODE_BATCHED>,
-                         (const void*)k_pie_full<N, MODE_GRAD>},
-                        sizeof(float2) * (N + N * Fft<N>::S) + sizeof(double) * kWarps};
-}
-
-const FullPieKernels g_full_pie[] = {make_full_pie<16>(), make_full_pie<32>(), make_full_pie<64>(),
-                                     make_full_pie<128>()};
-
 int grid_for(long long work) {
   long long g = (work + kThreads - 1) / kThreads;
   long long cap = 8LL * pfth::sm_count();
@@ -398,7 +131,10 @@ struct pie_ctx {
   int n = 0, npos = 0, H = 0, W = 0, M = 0;
   pft_plan plan;
   bool have_plan = false;
-  int pft_kid = -1, full_kid = -1;
+  bool have_full = false;
+  // kernels per [transform][mode][log2 cluster size] with their resident-CTA capacity
+  PieKernel kern[2][3][4];
+  long long cap[2][3][4] = {};
   float2* d_probe = nullptr;
   float probe_max2 = 0.f;
   int2* d_pos = nullptr;
@@ -414,15 +150,35 @@ struct pie_ctx {
   float2* d_acc = nullptr;
   double* d_red = nullptr;     // [8]
   double* h_red = nullptr;     // pinned [8]
-  int per_sm[2][3] = {};       // occupancy of the PFT / full kernels per mode
 };
 
 namespace {
 
-int prepare_kernel(const void* fn, size_t smem, int* per_sm) {
-  PFT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  PFT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kThreads, smem));
-  if (*per_sm < 1) return pfth::set_error(PFT_ERR_UNSUPPORTED, "PIE kernel does not fit on an SM");
+// Sets the shared-memory limit of a kernel and returns how many of its CTAs
+// can be resident at once (clusters x cluster size for clustered kernels).
+int prepare_kernel(const PieKernel& k, long long* cap) {
+  PFT_CUDA_TRY(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+  if (k.cluster == 1) {
+    int per_sm = 0;
+    PFT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem));
+    *cap = (long long)per_sm * pfth::sm_count();
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(k.cluster * 64);
+    cfg.blockDim = dim3(k.threads);
+    cfg.dynamicSmemBytes = k.smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = k.cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    PFT_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, k.fn, &cfg));
+    *cap = (long long)nclusters * k.cluster;
+  }
+  if (*cap < 1) return pfth::set_error(PFT_ERR_UNSUPPORTED, "PIE kernel does not fit on an SM");
   return PFT_OK;
 }
 
@@ -461,23 +217,46 @@ void colour_positions(pie_ctx* c) {
   for (int k = 0; k < ncol; ++k) c->col_off[k + 1] += c->col_off[k];
 }
 
+// Launches the fused kernel for `a.count` positions. Coloured sweeps pick the
+// largest cluster size whose CTAs for all positions of the colour fit on the
+// GPU at once; the other modes run one CTA per position.
 int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) {
   if (a.count <= 0) return PFT_OK;
-  if (transform == PIE_TRANSFORM_PFT) {
-    const PftPieKernels& K = g_pft_pie[c->pft_kid];
-    int grid = std::min(a.count, c->per_sm[0][mode] * pfth::sm_count());
-    PftConst cst = c->plan.cst;
-    const float2* W = c->plan.d_W;
-    const float2* tw = c->plan.d_twp;
-    void* args[] = {(void*)&a, (void*)&cst, (void*)&W, (void*)&tw};
-    PFT_CUDA_TRY(cudaLaunchKernel(K.k[mode], dim3(grid), dim3(kThreads), args, K.smem, st));
+  const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
+  int ci = 0;
+  if (mode == MODE_COLOURED)
+    for (int q = 3; q >= 1; --q)
+      if (c->kern[t][mode][q].fn && (long long)a.count * (1 << q) <= c->cap[t][mode][q]) {
+        ci = q;
+        break;
+      }
+  const PieKernel& k = c->kern[t][mode][ci];
+  if (!k.fn) return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for this transform and mode");
+  const long long clusters = std::min<long long>(a.count, std::max<long long>(1, c->cap[t][mode][ci] / k.cluster));
+  const dim3 grid((unsigned)(clusters * k.cluster));
+  PftConst cst = c->plan.cst;
+  const float2* W = c->plan.d_W;
+  const float2* tw = t == 0 ? c->plan.d_twp : pfth::twiddles(c->n);
+  if (!tw) return PFT_ERR_CUDA;
+  void* args_pft[] = {(void*)&a, (void*)&cst, (void*)&W, (void*)&tw};
+  void* args_full[] = {(void*)&a, (void*)&tw};
+  void** args = t == 0 ? args_pft : args_full;
+  if (k.cluster == 1) {
+    PFT_CUDA_TRY(cudaLaunchKernel(k.fn, grid, dim3(k.threads), args, k.smem, st));
   } else {
-    const FullPieKernels& K = g_full_pie[c->full_kid];
-    int grid = std::min(a.count, c->per_sm[1][mode] * pfth::sm_count());
-    const float2* tw = pfth::twiddles(c->n);
-    if (!tw) return PFT_ERR_CUDA;
-    void* args[] = {(void*)&a, (void*)&tw};
-    PFT_CUDA_TRY(cudaLaunchKernel(K.k[mode], dim3(grid), dim3(kThreads), args, K.smem, st));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(k.threads);
+    cfg.dynamicSmemBytes = k.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = k.cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    PFT_CUDA_TRY(cudaLaunchKernelExC(&cfg, k.fn, args));
   }
   return PFT_OK;
 }
@@ -556,21 +335,30 @@ int pie_ctx_create(pie_ctx** out, const pie_problem* pb, const void* probe, cons
   // PFT plan and kernels
   PIE_TRY(pfth::build_plan(&c->plan, n, M, pb->p, pb->eps > 0 ? pb->eps : 1e-7, 0));
   c->have_plan = true;
-  for (int i = 0; i < (int)(sizeof(g_pft_pie) / sizeof(g_pft_pie[0])); ++i)
-    if (g_pft_pie[i].P == c->plan.p1 && g_pft_pie[i].Q == c->plan.q1 && g_pft_pie[i].MP == M / c->plan.p1)
-      c->pft_kid = i;
-  if (c->pft_kid < 0) {
-    pie_ctx_destroy(c);
-    return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for n=%d M=%d", n, M);
+  {
+    const int P = c->plan.p1, Q = c->plan.q1, MP = M / c->plan.p1;
+    bool any = false;
+    for (int mode = 0; mode < 3; ++mode)
+      for (int q = 0; q < 4; ++q) {
+        PieKernel k = pfth::pie_pft_kernel(P, Q, MP, mode, 1 << q);
+        if (k.fn) {
+          PIE_TRY(prepare_kernel(k, &c->cap[0][mode][q]));
+          c->kern[0][mode][q] = k;
+          any = true;
+        }
+        PieKernel f = pfth::pie_full_kernel(n, mode, 1 << q);
+        if (f.fn) {
+          PIE_TRY(prepare_kernel(f, &c->cap[1][mode][q]));
+          c->kern[1][mode][q] = f;
+          c->have_full = true;
+        }
+      }
+    if (!any) {
+      pie_ctx_destroy(c);
+      return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for n=%d M=%d", n, M);
+    }
   }
-  for (int i = 0; i < (int)(sizeof(g_full_pie) / sizeof(g_full_pie[0])); ++i)
-    if (g_full_pie[i].N == n) c->full_kid = i;
-  for (int m = 0; m < 3; ++m) {
-    PIE_TRY(prepare_kernel(g_pft_pie[c->pft_kid].k[m], g_pft_pie[c->pft_kid].smem, &c->per_sm[0][m]));
-    if (c->full_kid >= 0)
-      PIE_TRY(prepare_kernel(g_full_pie[c->full_kid].k[m], g_full_pie[c->full_kid].smem, &c->per_sm[1][m]));
-  }
-  if (c->full_kid >= 0 && !pfth::twiddles(n)) {
+  if (c->have_full && !pfth::twiddles(n)) {
     pie_ctx_destroy(c);
     return PFT_ERR_CUDA;
   }
@@ -635,7 +423,7 @@ int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stat
   if (!c || !object) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
   if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
     return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
-  if (transform == PIE_TRANSFORM_FULL && c->full_kid < 0)
+  if (transform == PIE_TRANSFORM_FULL && !c->have_full)
     return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n in {16, 32, 64, 128}, not %d", c->n);
   cudaStream_t st = (cudaStream_t)stream;
   const long long HW = (long long)c->H * c->W;

@@ -1,0 +1,56 @@
+// Instantiations of the full-FFT variant of the fused PIE kernel.
+#include <vector>
+
+#include "pie_kernels.cuh"
+
+using namespace pftk;
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Entry {
+  int N, mode, C;
+  PieKernel k;
+};
+
+template <int N, int MODE, int C>
+void add(std::vector<Entry>& v) {
+  if constexpr (PieFullShape<N, C>::VALID) {
+    PieKernel k;
+    k.fn = (const void*)k_pie_full<N, MODE, C, kThreads>;
+    k.smem = PieFullShape<N, C>::SMEM;
+    k.cluster = C;
+    k.threads = kThreads;
+    v.push_back(Entry{N, MODE, C, k});
+  }
+}
+
+template <int N>
+void add_size(std::vector<Entry>& v) {
+  add<N, MODE_COLOURED, 1>(v);
+  add<N, MODE_COLOURED, 2>(v);
+  add<N, MODE_COLOURED, 4>(v);
+  add<N, MODE_COLOURED, 8>(v);
+  add<N, MODE_BATCHED, 1>(v);
+}
+
+std::vector<Entry> build_table() {
+  std::vector<Entry> v;
+  add_size<16>(v);
+  add_size<32>(v);
+  add_size<64>(v);
+  add_size<128>(v);
+  return v;
+}
+
+}  // namespace
+
+namespace pfth {
+PieKernel pie_full_kernel(int N, int mode, int C) {
+  static const std::vector<Entry> table = build_table();
+  for (const Entry& e : table)
+    if (e.N == N && e.mode == mode && e.C == C) return e.k;
+  return PieKernel{};
+}
+}  // namespace pfth

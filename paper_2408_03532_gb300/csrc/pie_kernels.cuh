@@ -1,0 +1,343 @@
+// Fused per-position PIE kernels (Section 2.1, Eq. pie_update with Eq. 3).
+//
+// One scan position j is processed by a thread-block cluster of C CTAs:
+//   1. rows: CTA c forms the exit wave psi = w . Q_j z on rows [c n/C, (c+1) n/C)
+//      and transforms them along axis 2 (PFT rows or FFT rows); each result is
+//      written straight into the shared memory of the CTA that owns its column
+//      (distributed shared memory), so the n x M (or n x n) intermediate is
+//      redistributed without touching global memory;
+//   2. cluster barrier;
+//   3. columns: CTA c transforms its M/C (or n/C) columns along axis 1, applies
+//      the modulus projection R = Psi - d . sgn(Psi) on its part of the
+//      spectrum (accumulating ||R||^2 for Eq. 4), and runs the adjoint column
+//      transform; results go back to the row owners;
+//   4. cluster barrier;
+//   5. rows: the adjoint row transform gives A^H R on CTA c's rows, and the
+//      object update z -= beta conj(w) / max|w|^2 . A^H R / n^2 is applied.
+// With C = 1 the cluster is one CTA and the two exchange buffers alias. The
+// barriers are the hardware cluster barrier; there is no spin wait.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "fft_core.cuh"
+#include "pft_core.cuh"
+
+namespace pftk {
+
+namespace cg = cooperative_groups;
+
+enum { MODE_COLOURED = 0, MODE_BATCHED = 1, MODE_GRAD = 2 };
+
+struct PieArgs {
+  float2* obj;              // object [H][W] (written in MODE_COLOURED)
+  const float2* objr;       // object read pointer (= obj, or the gradient's input)
+  long long obj_w;
+  const float2* probe;      // [n][n]
+  const int2* pos;          // [N] top-left (row, col)
+  const int* list;          // positions to process (nullptr = 0..count-1)
+  int count;
+  const float* dat;         // amplitudes: [N][M][M] centred crop, or [N][n][n] FFT order
+  float coef;               // update scale
+  float2* acc;              // MODE_BATCHED: sum conj(w) dpsi; MODE_GRAD: grad_obj
+  float2* gprobe;           // MODE_GRAD: grad_probe (may be null)
+  double* red;              // red[0] += sum ||R||^2 (MODE_GRAD: the loss)
+};
+
+template <int C>
+struct Cluster {
+  __device__ __forceinline__ static unsigned rank() {
+    if constexpr (C == 1) return 0;
+    else return cg::this_cluster().block_rank();
+  }
+  __device__ __forceinline__ static void sync() {
+    if constexpr (C == 1) __syncthreads();
+    else cg::this_cluster().sync();
+  }
+  template <class T>
+  __device__ __forceinline__ static T* map(T* p, unsigned r) {
+    if constexpr (C == 1) return p;
+    else return cg::this_cluster().map_shared_rank(p, r);
+  }
+};
+
+// Modulus-projection residual (Eq. 3) and its contribution to the objective.
+template <int MODE>
+__device__ __forceinline__ float2 residual(float2 Psi, float d, double& acc) {
+  const float m2 = cabs2(Psi);
+  if (MODE == MODE_GRAD) {
+    // sgn(0) = 0; the gradient of sum (|Psi| - d)^2 is 2 R
+    if (m2 > 0.f) {
+      const float m = sqrtf(m2);
+      const float diff = m - d;
+      acc += (double)diff * (double)diff;
+      return cscale(Psi, 2.f * diff / m);
+    }
+    acc += (double)d * (double)d;
+    return make_float2(0.f, 0.f);
+  }
+  // theta(0) = 0: a zero coefficient is replaced by d
+  float2 R;
+  if (m2 > 0.f) {
+    const float m = sqrtf(m2);
+    R = cscale(Psi, 1.f - d / m);
+  } else {
+    R = make_float2(-d, 0.f);
+  }
+  acc += (double)cabs2(R);
+  return R;
+}
+
+template <int MODE>
+__device__ __forceinline__ void apply_update(const PieArgs& a, long long oidx, float2 w, float2 dpsi, int pidx) {
+  if (MODE == MODE_COLOURED) {
+    float2 o = a.obj[oidx];
+    const float2 u = cmulc(dpsi, w);  // conj(w) dpsi
+    o.x = fmaf(-a.coef, u.x, o.x);
+    o.y = fmaf(-a.coef, u.y, o.y);
+    a.obj[oidx] = o;
+  } else if (MODE == MODE_BATCHED) {
+    atomicAdd(a.acc + oidx, cscale(cmulc(dpsi, w), a.coef));
+  } else {
+    atomicAdd(a.acc + oidx, cmulc(dpsi, w));
+    if (a.gprobe) atomicAdd(a.gprobe + pidx, cmulc(dpsi, a.objr[oidx]));
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ void block_accumulate(double v, double* red_smem, double* out) {
+  double s = block_sum(v, red_smem);
+  if (threadIdx.x == 0 && s != 0.0) atomicAdd(out, s);
+}
+
+// ------------------------------------------------------------- PFT variant
+template <int P, int Q, int MP, int C>
+struct PiePftShape {
+  static constexpr int N = P * Q, M = MP * P, G = 32 / P;
+  static constexpr int RN = N / C;   // rows owned by one CTA
+  static constexpr int CM = M / C;   // columns owned by one CTA
+  static constexpr bool VALID = (N % C == 0) && (M % C == 0) && CM >= 1 && (RN % G == 0) &&
+                                (CM % G == 0) && (RN % Q == 0);
+  // column slice of Y, all rows: element (t, u) at t * SYT + u + u / Q
+  static constexpr int SYT_BASE = N + N / Q;
+  static constexpr int SYT = SYT_BASE + (((8 - SYT_BASE % 16) + 16) % 16);
+  static constexpr int ZS = CM + 1;  // Z: [M][CM + 1]
+  static constexpr int SG = M + 8;   // G: [RN][M + 8]
+  static constexpr int OFF_W1 = 0;
+  static constexpr int OFF_W2 = OFF_W1 + RMAX * M;
+  static constexpr int OFF_TW = OFF_W2 + RMAX * M;
+  static constexpr int OFF_Y = OFF_TW + 16;
+  static constexpr int Y_SIZE = CM * SYT;
+  static constexpr int G_SIZE = RN * SG;
+  static constexpr int OFF_G = (C == 1) ? OFF_Y : OFF_Y + Y_SIZE;  // alias for one CTA
+  static constexpr int OFF_Z = (C == 1) ? OFF_Y + (Y_SIZE > G_SIZE ? Y_SIZE : G_SIZE) : OFF_G + G_SIZE;
+  static constexpr int OFF_RED = OFF_Z + M * ZS;
+  static constexpr size_t SMEM = sizeof(float2) * (OFF_RED + 16);
+};
+
+template <int P, int Q, int MP, int MODE, int C, int NT>
+__global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant__ PftConst c,
+                                                const float2* __restrict__ gW, const float2* __restrict__ gtw) {
+  using S = PiePftShape<P, Q, MP, C>;
+  using T = Pft1D<P, Q, MP>;
+  using CL = Cluster<C>;
+  constexpr int N = S::N, M = S::M, G = S::G, RN = S::RN, CM = S::CM, NW = NT / 32;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* sW1 = sm + S::OFF_W1;
+  float2* sW2 = sm + S::OFF_W2;
+  float2* stw = sm + S::OFF_TW;
+  float2* sY = sm + S::OFF_Y;
+  float2* sG = sm + S::OFF_G;
+  float2* sZ = sm + S::OFF_Z;
+  double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
+  for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) sm[i] = gW[i];
+  for (int i = threadIdx.x; i < P / 2; i += NT) stw[i] = gtw[i];
+  const unsigned rank = CL::rank();
+  CL::sync();  // every CTA of the cluster has started before any remote store
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = lane % P, g = lane / P;
+  const int r0 = rank * RN;
+  for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
+    const int j = a.list ? a.list[it] : it;
+    const int2 rc = a.pos[j];
+    const long long obase = (long long)rc.x * a.obj_w + rc.y;
+    // 1. rows (axis 2) of the exit wave -> column owners
+    for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
+      const int u = r0 + u0 + g;
+      float2 xv[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const int v = Q * k + l;
+        xv[l] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
+      }
+      T::forward(xv, k, c.bh[1], sW2, stw, [&](int t, float2 val) {
+        float2* dst = CL::map(sY, (unsigned)(t / CM));
+        dst[(t % CM) * S::SYT + u + u / Q] = val;
+      });
+    }
+    CL::sync();
+    // 3a. columns (axis 1) of this CTA's slice
+    for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
+      const int tl = cs0 + g;
+      float2 xv[Q];
+#pragma unroll
+      for (int l = 0; l < Q; ++l) xv[l] = sY[tl * S::SYT + Q * k + l + k];
+      T::forward(xv, k, c.bh[0], sW1, stw, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
+    }
+    __syncthreads();
+    // 3b. modulus projection on the M x CM coefficients
+    const float* dj = a.dat + (long long)j * (M * M) + rank * CM;
+    double part = 0.0;
+    for (int i = threadIdx.x; i < M * CM; i += NT) {
+      float2* z = sZ + (i / CM) * S::ZS + (i % CM);
+      *z = residual<MODE>(*z, __ldg(dj + (i / CM) * M + (i % CM)), part);
+    }
+    block_accumulate<NT>(part, sred, a.red);
+    __syncthreads();
+    // 3c. adjoint columns -> row owners
+    for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
+      const int tl = cs0 + g;
+      float2 xv[Q];
+      T::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, c.bh[0], sW1, stw, xv);
+      const int u0 = Q * k;
+      float2* dst = CL::map(sG, (unsigned)(u0 / RN));
+      const int tg = rank * CM + tl;
+#pragma unroll
+      for (int l = 0; l < Q; ++l) dst[(u0 % RN + l) * S::SG + tg] = xv[l];
+    }
+    CL::sync();
+    // 5. adjoint rows and the object update
+    for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
+      const int ul = u0 + g, u = r0 + ul;
+      float2 xv[Q];
+      T::adjoint([&](int t) { return sG[ul * S::SG + t]; }, k, c.bh[1], sW2, stw, xv);
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const int v = Q * k + l;
+        apply_update<MODE>(a, obase + (long long)u * a.obj_w + v, __ldg(a.probe + u * N + v), xv[l], u * N + v);
+      }
+    }
+    if constexpr (C == 1) __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ FFT variant
+template <int N, int C>
+struct PieFullShape {
+  using F = Fft<N>;
+  static constexpr int RN = N / C, CN = N / C;
+  static constexpr bool VALID = (N % C == 0) && RN >= 1 && (RN % F::G == 0) && (CN % F::G == 0);
+  static constexpr int SCS = CN + 1;  // column slice: [N][CN + 1]
+  static constexpr int SRS = N + 1;   // row slice: [RN][N + 1]
+  static constexpr int OFF_TW = 0;
+  static constexpr int OFF_C = N;
+  static constexpr int OFF_R = (C == 1) ? OFF_C : OFF_C + N * SCS;  // alias for one CTA
+  static constexpr int OFF_RED = (C == 1) ? OFF_C + N * SCS : OFF_R + RN * SRS;
+  static constexpr size_t SMEM = sizeof(float2) * (OFF_RED + 16);
+};
+
+template <int N, int MODE, int C, int NT>
+__global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __restrict__ gtw) {
+  using S = PieFullShape<N, C>;
+  using F = Fft<N>;
+  using CL = Cluster<C>;
+  constexpr int L = F::L, E = F::E, G = F::G, RN = S::RN, CN = S::CN, NW = NT / 32;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* tw = sm + S::OFF_TW;
+  float2* sC = sm + S::OFF_C;
+  float2* sR = sm + S::OFF_R;
+  double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
+  for (int i = threadIdx.x; i < N; i += NT) tw[i] = gtw[i];
+  const unsigned rank = CL::rank();
+  CL::sync();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l = lane % L, g = lane / L;
+  const int r0 = rank * RN, c0 = rank * CN;
+  for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
+    const int j = a.list ? a.list[it] : it;
+    const int2 rc = a.pos[j];
+    const long long obase = (long long)rc.x * a.obj_w + rc.y;
+    // 1. FFT of this CTA's rows of the exit wave -> column-slot owners
+    for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
+      const int u = r0 + u0 + g;
+      float2 x[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = l + L * e;
+        x[e] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
+      }
+      F::fwd(x, l, tw);
+#pragma unroll
+      for (int p = 0; p < E; ++p) {
+        const int s = p * L + l;
+        CL::map(sC, (unsigned)(s / CN))[u * S::SCS + s % CN] = x[p];
+      }
+    }
+    CL::sync();
+    // 3a. FFT of the local slot columns (rows in natural order -> slot order)
+    for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
+      const int b = b0 + g;
+      float2 x[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) x[e] = sC[(l + L * e) * S::SCS + b];
+      F::fwd(x, l, tw);
+#pragma unroll
+      for (int p = 0; p < E; ++p) sC[(p * L + l) * S::SCS + b] = x[p];
+    }
+    __syncthreads();
+    // 3b. modulus projection
+    const float* dj = a.dat + (long long)j * (N * N);
+    double part = 0.0;
+    for (int i = threadIdx.x; i < N * CN; i += NT) {
+      const int sa = i / CN, sb = i % CN;
+      float2* z = sC + sa * S::SCS + sb;
+      *z = residual<MODE>(*z, __ldg(dj + F::freq_of_slot(sa) * N + F::freq_of_slot(c0 + sb)), part);
+    }
+    block_accumulate<NT>(part, sred, a.red);
+    __syncthreads();
+    // 3c. adjoint FFT of the local columns -> row owners (natural row order)
+    for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
+      const int b = b0 + g;
+      float2 x[E];
+#pragma unroll
+      for (int p = 0; p < E; ++p) x[p] = sC[(p * L + l) * S::SCS + b];
+      F::adj(x, l, tw);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int u = l + L * e;
+        CL::map(sR, (unsigned)(u / RN))[(u % RN) * S::SRS + c0 + b] = x[e];
+      }
+    }
+    CL::sync();
+    // 5. adjoint FFT of this CTA's rows and the object update
+    for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
+      const int ul = u0 + g, u = r0 + ul;
+      float2 x[E];
+#pragma unroll
+      for (int p = 0; p < E; ++p) x[p] = sR[ul * S::SRS + p * L + l];
+      F::adj(x, l, tw);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = l + L * e;
+        apply_update<MODE>(a, obase + (long long)u * a.obj_w + v, __ldg(a.probe + u * N + v), x[e], u * N + v);
+      }
+    }
+    if constexpr (C == 1) __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- registry
+struct PieKernel {
+  const void* fn = nullptr;
+  size_t smem = 0;
+  int cluster = 1;
+  int threads = 256;
+};
+
+}  // namespace pftk
+
+namespace pfth {
+// PIE kernels for a (transform, shape, mode, cluster size); fn == nullptr if not built.
+pftk::PieKernel pie_pft_kernel(int P, int Q, int MP, int mode, int C);
+pftk::PieKernel pie_full_kernel(int N, int mode, int C);
+}  // namespace pfth
