@@ -150,6 +150,16 @@ struct pie_ctx {
   float2* d_acc = nullptr;
   double* d_red = nullptr;     // [8]
   double* h_red = nullptr;     // pinned [8]
+  // captured sweeps, replayed on the caller's stream
+  struct Graph {
+    const void* obj;
+    int transform;
+    double beta;
+    bool stats;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
@@ -283,6 +293,8 @@ int pie_ctx_destroy(pie_ctx* c) {
   cudaFree(c->d_acc);
   cudaFree(c->d_red);
   if (c->h_red) cudaFreeHost(c->h_red);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return PFT_OK;
 }
@@ -396,6 +408,7 @@ int pie_ctx_create(pie_ctx** out, const pie_problem* pb, const void* probe, cons
   PIE_CUDA(cudaMalloc(&c->d_prev, sizeof(float2) * HW));
   PIE_CUDA(cudaMalloc(&c->d_red, sizeof(double) * 8));
   PIE_CUDA(cudaMallocHost(&c->h_red, sizeof(double) * 8));
+  PIE_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   if (pb->mode == PIE_MODE_BATCHED) PIE_CUDA(cudaMalloc(&c->d_acc, sizeof(float2) * HW));
   PIE_CUDA(cudaMemsetAsync(c->d_inv_illum, 0, sizeof(float) * HW, st));
   PIE_CUDA(cudaMemsetAsync(c->d_red, 0, sizeof(double) * 8, st));
@@ -419,15 +432,15 @@ int pie_ctx_colours(const pie_ctx* c, int* ncolours, int32_t* colour_of) {
   return PFT_OK;
 }
 
-int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stats* stats, void* stream) {
-  if (!c || !object) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
-  if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
-    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
-  if (transform == PIE_TRANSFORM_FULL && !c->have_full)
-    return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n in {16, 32, 64, 128}, not %d", c->n);
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// Enqueues one sweep on `st`: statistics buffers, the kernels of every colour
+// (or the batched kernel and its update), and with `stats` the FP64 norms and
+// their copy to pinned host memory.
+int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st) {
   const long long HW = (long long)c->H * c->W;
-  float2* obj = (float2*)object;
   if (stats) PFT_CUDA_TRY(cudaMemcpyAsync(c->d_prev, obj, sizeof(float2) * HW, cudaMemcpyDeviceToDevice, st));
   PFT_CUDA_TRY(cudaMemsetAsync(c->d_red, 0, sizeof(double) * 8, st));
   const float n2 = (float)c->n * (float)c->n;
@@ -464,7 +477,57 @@ int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stat
     k_diff_norms<<<grid_for(HW), kThreads, 0, st>>>(obj, c->d_prev, HW, c->d_red + 1);
     PFT_CUDA_TRY(cudaGetLastError());
     PFT_CUDA_TRY(cudaMemcpyAsync(c->h_red, c->d_red, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+  }
+  return PFT_OK;
+}
+
+// Returns the executable graph of a sweep, capturing it on first use.
+int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaGraphExec_t* out) {
+  for (auto& g : c->graphs)
+    if (g.obj == obj && g.transform == transform && g.beta == beta && g.stats == stats) {
+      *out = g.exec;
+      return PFT_OK;
+    }
+  PFT_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_sweep(c, obj, transform, beta, stats, c->cap_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+  if (rc != PFT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return pfth::cuda_error(e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return pfth::cuda_error(e, "cudaGraphInstantiate");
+  if (c->graphs.size() >= 8) {
+    cudaGraphExecDestroy(c->graphs.front().exec);
+    c->graphs.erase(c->graphs.begin());
+  }
+  c->graphs.push_back({obj, transform, beta, stats, exec});
+  *out = exec;
+  return PFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stats* stats, void* stream) {
+  if (!c || !object) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
+  if (transform == PIE_TRANSFORM_FULL && !c->have_full)
+    return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n in {16, 32, 64, 128}, not %d", c->n);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaGraphExec_t exec = nullptr;
+  int rc = sweep_graph(c, (float2*)object, transform, beta, stats != nullptr, &exec);
+  if (rc != PFT_OK) return rc;
+  PFT_CUDA_TRY(cudaGraphLaunch(exec, st));
+  if (stats) {
     PFT_CUDA_TRY(cudaStreamSynchronize(st));
+    const double n2 = (double)c->n * (double)c->n;
     stats->phi = c->h_red[0] / ((double)c->npos * n2);
     stats->rel_change = c->h_red[2] > 0 ? std::sqrt(c->h_red[1] / c->h_red[2]) : 0.0;
     if (!std::isfinite(stats->phi) || !std::isfinite(stats->rel_change))
