@@ -233,6 +233,29 @@ int pie_nrmse(pie_ctx* ctx, const void* object, const void* truth, double* out, 
 int pie_amp_loss_grad(pie_ctx* ctx, const void* object, const void* probe, void* grad_obj,
                       void* grad_probe, double* loss, void* stream);
 
+/* ---- allocation-free error reduction ------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory when they need the error: code being recorded into a
+ * CUDA graph (cudaMalloc / cudaFree are not allowed during stream capture),
+ * latency-critical loops (allocation can synchronise the whole device), and
+ * plug-ins in a host framework that owns every device allocation.
+ *
+ * pie_nrmse_noalloc(object, truth, mask, count, out, stream)
+ *   Same quantity as pie_nrmse, min_phi ||e^{i phi} z - truth|| / ||truth||,
+ *   over the elements whose mask byte is non-zero (mask == NULL: all).
+ *   object, truth: device complex [count]; mask: device uint8 [count] or NULL;
+ *   out: host double. 1 <= count <= 16,777,216 (a 4096 x 4096 object); larger
+ *   counts return PFT_ERR_INVALID_ARG. Synchronises `stream`.
+ *   It calls no allocator: its partial sums live in a fixed 128 KiB array
+ *   compiled into the library (held on every GPU that loads the library until
+ *   the process exits). The first call on a device looks up that array's
+ *   device address, so make that first call before any stream capture. All
+ *   calls share the array: calls that overlap on the GPU (other streams, other
+ *   host threads) race and must be serialised by the caller.
+ */
+int pie_nrmse_noalloc(const void* object, const void* truth, const uint8_t* mask, int64_t count,
+                      double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,7 @@ def load() -> ctypes.CDLL:
         "warm_start_then_refine": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse": (ctypes.c_int, [_P, _P, _P, _P, _P]),
         "pie_amp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+        "pie_nrmse_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -227,6 +228,25 @@ def fft_crop(x, M: int, out=None, stream=None):
     batch = int(np.prod(lead)) if len(lead) else 1
     _check(load().pft_fft_crop(_ptr(x), _ptr(out), n, M, batch, _stream(stream)))
     return out
+
+
+def nrmse_noalloc(obj, truth, mask=None, stream=None) -> float:
+    """Phase-aligned error of obj against truth over mask (uint8, or None for
+    all elements), computed without any device allocation: for callers that
+    cannot allocate at that moment (inside stream capture, in latency-critical
+    loops, or under a framework that owns all device memory). The library keeps
+    the partial sums in one fixed device array, so calls must not overlap."""
+    import torch
+    _need(obj, torch.complex64, None, "obj")
+    _need(truth, torch.complex64, tuple(obj.shape), "truth")
+    if mask is not None:
+        _need(mask, torch.uint8, None, "mask")
+        if mask.numel() != obj.numel():
+            raise ValueError("mask must have one byte per element")
+    out = ctypes.c_double()
+    _check(load().pie_nrmse_noalloc(_ptr(obj), _ptr(truth), _ptr(mask), obj.numel(), ctypes.byref(out),
+                                    _stream(stream)))
+    return out.value
 
 
 # --------------------------------------------------------------------- PIE
