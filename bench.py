@@ -137,6 +137,13 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def aggregate(frames_per_rank_step: int, ms_local: float, world: int) -> tuple[float, float]:
+    """(ms per step, whole-job frames/s): the slowest rank's step time, and the
+    frames all ranks processed per step divided by it (weak scaling)."""
+    ms = max_over_ranks(ms_local, world)
+    return ms, world * frames_per_rank_step / (ms / 1e3)
+
+
 def barrier(world: int) -> None:
     if world > 1:
         import torch.distributed as dist
@@ -260,6 +267,7 @@ def main() -> None:
     ctx = pft.PieContext((H, W), probe, P["pos"], inten, M=M, mode=mode)
     del inten
     ncol = int(ctx.colours().max()) + 1
+    tuning = ctx.info()
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -290,9 +298,8 @@ def main() -> None:
     t_pft = [e[0].elapsed_time(e[1]) for e in ev]
     t_full = [e[1].elapsed_time(e[2]) for e in ev]
     ms_local = (sum(t_pft) + sum(t_full)) / args.steps
-    ms = max_over_ranks(ms_local, world)
     frames_per_step = 2 * len(P["pos"])
-    value = world * frames_per_step / (ms / 1e3)
+    ms, value = aggregate(frames_per_step, ms_local, world)
 
     # kernel-only sweep times (no statistics, no host synchronisation inside)
     kev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -365,7 +372,8 @@ def main() -> None:
                         "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                 "gpu_launches": 2 * launches_per_sweep * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "time_to_target": ttt, "pft_batch": pft_batch, "wall_s": wall, "colours": ncol}
+                "time_to_target": ttt, "pft_batch": pft_batch, "wall_s": wall, "colours": ncol,
+                "autotune": tuning}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

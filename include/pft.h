@@ -170,6 +170,9 @@ typedef struct pie_problem {
   int mode;              /* PIE_MODE_*                                         */
   int path;              /* PFT_PATH_* for the partial transform               */
   double delta_rel;      /* batched mode: delta = delta_rel * max illumination */
+  int autotune;          /* 1: time every built kernel variant (CTAs per position)
+                            on a scratch object at creation and keep the fastest;
+                            0: pick by occupancy                                  */
 } pie_problem;
 
 typedef struct pie_stats {
@@ -180,6 +183,18 @@ typedef struct pie_stats {
 int pie_ctx_create(pie_ctx** out, const pie_problem* problem, const void* probe,
                    const int32_t* positions, const float* intensities, void* stream);
 int pie_ctx_destroy(pie_ctx* ctx);
+
+/* What the context chose: colours, PFT factorisation, and the CTAs per
+ * position of the PFT and full-FFT sweeps picked by the autotuner (0 when not
+ * tuned: chosen per launch by occupancy) with the sweep time it measured. */
+typedef struct pie_ctx_info {
+  int ncolours;
+  int p, q, r;
+  int cluster_pft, cluster_full;
+  double sweep_ms_pft, sweep_ms_full;
+} pie_ctx_info;
+
+int pie_ctx_info_get(const pie_ctx* ctx, pie_ctx_info* info);
 
 /* Number of colours of the greedy colouring (positions in index order take
  * the smallest colour unused by an earlier overlapping patch), and the

@@ -66,17 +66,30 @@ __host__ __device__ __forceinline__ int bitrev(int k) {
 }
 
 // ------------------------------------------------------- lane DFT network
+// Stage table of an L-lane network: entry (h - 1) + m holds w_{2h}^m =
+// e^{-2 pi i m / (2h)} for h = 1, 2, 4, ..., L/2 and m < h (L - 1 entries), so
+// the lanes of one stage read consecutive entries (no bank conflicts).
+// src[i] = e^{-2 pi i i / NS}; NS is a multiple of L.
+template <int L>
+__device__ __forceinline__ void fill_stage_table(float2* tws, const float2* __restrict__ src, int NS) {
+  for (int i = threadIdx.x; i < L - 1; i += blockDim.x) {
+    int h = 1;
+    while (2 * h <= i + 1) h *= 2;
+    tws[i] = src[(i + 1 - h) * (NS / (2 * h))];
+  }
+}
+
 // L-point DFT across groups of L consecutive lanes (L <= 32, a power of two).
 // In: lane k (= lane % L) holds x[k]. Out: lane k holds X[bitrev_L(k)], with
 // X[f] = sum_k x[k] w^{f k}, w = e^{-2 pi i / L} (conjugated when INV).
-// tw[m * TS] = e^{-2 pi i m / L}, m < L / 2 (shared memory; TS = table stride).
-template <int L, bool INV, int TS = 1>
-__device__ __forceinline__ float2 lane_dif(float2 v, int k, const float2* __restrict__ tw) {
+// tws: the stage table above (shared memory).
+template <int L, bool INV>
+__device__ __forceinline__ float2 lane_dif(float2 v, int k, const float2* __restrict__ tws) {
 #pragma unroll
   for (int h = L / 2; h >= 1; h >>= 1) {
     float2 o = shfl_xor2(v, h);
     if (k & h) {
-      float2 w = tw[(k & (h - 1)) * (L / (2 * h)) * TS];
+      float2 w = tws[h - 1 + (k & (h - 1))];
       if (INV) w.y = -w.y;
       v = cmul(csub(o, v), w);
     } else {
@@ -88,13 +101,13 @@ __device__ __forceinline__ float2 lane_dif(float2 v, int k, const float2* __rest
 
 // Exact adjoint of lane_dif<L, INV>: lane k holds Y[bitrev(k)] on entry and
 // sum_f conj(w)^{f k} Y[f] on exit (natural order).
-template <int L, bool INV, int TS = 1>
-__device__ __forceinline__ float2 lane_dif_adj(float2 v, int k, const float2* __restrict__ tw) {
+template <int L, bool INV>
+__device__ __forceinline__ float2 lane_dif_adj(float2 v, int k, const float2* __restrict__ tws) {
 #pragma unroll
   for (int h = 1; h <= L / 2; h <<= 1) {
     float2 s = v;
     if (k & h) {
-      float2 w = tw[(k & (h - 1)) * (L / (2 * h)) * TS];
+      float2 w = tws[h - 1 + (k & (h - 1))];
       if (!INV) w.y = -w.y;
       s = cmul(v, w);
     }
@@ -103,6 +116,51 @@ __device__ __forceinline__ float2 lane_dif_adj(float2 v, int k, const float2* __
   }
   return v;
 }
+
+// The same network with each lane's twiddles and signs held in registers.
+// Lane k's twiddle and sign at every stage depend only on k, so they are
+// loaded once; each butterfly is then branch-free: two shuffles, d = o + sg v,
+// and a complex multiply by the lane's twiddle (1 for the lower lane, and
+// skipped at the last stage where every twiddle is 1).
+template <int L, bool INV>
+struct LaneNet {
+  static constexpr int S = ilog2<L>() > 0 ? ilog2<L>() : 1;
+  float2 w[S];
+  float sg[S];
+  __device__ __forceinline__ void init(int k, const float2* __restrict__ tws) {
+#pragma unroll
+    for (int s = 0; s < ilog2<L>(); ++s) {
+      const int h = L >> (s + 1);
+      const bool up = (k & h) != 0;
+      float2 t = up ? tws[h - 1 + (k & (h - 1))] : make_float2(1.f, 0.f);
+      if (INV) t.y = -t.y;
+      w[s] = t;
+      sg[s] = up ? -1.f : 1.f;
+    }
+  }
+  // = lane_dif<L, INV>
+  __device__ __forceinline__ float2 fwd(float2 v) const {
+#pragma unroll
+    for (int s = 0; s < ilog2<L>(); ++s) {
+      const int h = L >> (s + 1);
+      const float2 o = shfl_xor2(v, h);
+      const float2 d = make_float2(fmaf(sg[s], v.x, o.x), fmaf(sg[s], v.y, o.y));
+      v = (h == 1) ? d : cmul(d, w[s]);
+    }
+    return v;
+  }
+  // = lane_dif_adj<L, INV> (the exact adjoint of fwd)
+  __device__ __forceinline__ float2 adj(float2 v) const {
+#pragma unroll
+    for (int s = ilog2<L>() - 1; s >= 0; --s) {
+      const int h = L >> (s + 1);
+      const float2 t = (h == 1) ? v : cmulc(v, w[s]);
+      const float2 o = shfl_xor2(t, h);
+      v = make_float2(fmaf(sg[s], t.x, o.x), fmaf(sg[s], t.y, o.y));
+    }
+    return v;
+  }
+};
 
 // ---------------------------------------------------- register DFT network
 // E-point DFT over the registers of one thread (E a power of two <= 16).

@@ -28,11 +28,13 @@ __global__ void __launch_bounds__(kThreads) k_fft2(const float2* in, float2* out
   constexpr int L = F::L, E = F::E, G = F::G, S = F::S;
   extern __shared__ __align__(16) float2 sm[];
   float2* tw = sm;
-  float2* sF = sm + N;
-  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = gtw[i];
+  float2* sF = sm + F::TAB;
+  F::fill(tw, gtw);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l = lane % L, g = lane / L;
+  typename F::Net net;
+  F::init_net(net, l, tw);
   for (long long f = blockIdx.x; f < batch; f += gridDim.x) {
     const float2* src = in + f * (long long)(N * N);
     float2* dst = out + f * (long long)(N * N);
@@ -42,7 +44,7 @@ __global__ void __launch_bounds__(kThreads) k_fft2(const float2* in, float2* out
         float2 x[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = src[u * N + l + L * e];
-        F::fwd(x, l, tw);
+        F::fwd(x, l, tw, net);
 #pragma unroll
         for (int p = 0; p < E; ++p) sF[u * S + p * L + l] = x[p];
       }
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(kThreads) k_fft2(const float2* in, float2* out
         float2 x[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = sF[(l + L * e) * S + b];
-        F::fwd(x, l, tw);
+        F::fwd(x, l, tw, net);
 #pragma unroll
         for (int p = 0; p < E; ++p) sF[(p * L + l) * S + b] = x[p];
       }
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) k_fft2(const float2* in, float2* out
         float2 x[E];
 #pragma unroll
         for (int p = 0; p < E; ++p) x[p] = sF[(p * L + l) * S + b];
-        F::adj(x, l, tw);
+        F::adj(x, l, tw, net);
 #pragma unroll
         for (int e = 0; e < E; ++e) sF[(l + L * e) * S + b] = x[e];
       }
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(kThreads) k_fft2(const float2* in, float2* out
         float2 x[E];
 #pragma unroll
         for (int p = 0; p < E; ++p) x[p] = sF[u * S + p * L + l];
-        F::adj(x, l, tw);
+        F::adj(x, l, tw, net);
 #pragma unroll
         for (int e = 0; e < E; ++e) dst[u * N + l + L * e] = x[e];
       }
@@ -97,12 +99,14 @@ __global__ void __launch_bounds__(kThreads) k_fft_crop(const float2* __restrict_
   constexpr int SM = M + 1;
   extern __shared__ __align__(16) float2 sm[];
   float2* tw = sm;
-  float2* sR = sm + N;          // [N][M+1] rows after the row FFT, kept columns
+  float2* sR = sm + F::TAB;     // [N][M+1] rows after the row FFT, kept columns
   float2* sO = sR + N * SM;     // [M][M+1]
-  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = gtw[i];
+  F::fill(tw, gtw);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l = lane % L, g = lane / L;
+  typename F::Net net;
+  F::init_net(net, l, tw);
   for (long long f = blockIdx.x; f < batch; f += gridDim.x) {
     const float2* src = in + f * (long long)(N * N);
     for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_crop(const float2* __restrict_
       float2 x[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) x[e] = __ldg(src + u * N + l + L * e);
-      F::fwd(x, l, tw);
+      F::fwd(x, l, tw, net);
 #pragma unroll
       for (int p = 0; p < E; ++p) {
         const int ci = crop_index<N, M>(F::freq_of_slot(p * L + l));
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_crop(const float2* __restrict_
       float2 x[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) x[e] = sR[(l + L * e) * SM + ci];
-      F::fwd(x, l, tw);
+      F::fwd(x, l, tw, net);
 #pragma unroll
       for (int p = 0; p < E; ++p) {
         const int ri = crop_index<N, M>(F::freq_of_slot(p * L + l));
@@ -153,7 +157,7 @@ template <int N>
 int run_fft2(const void* in, void* out, long long batch, int inverse, cudaStream_t st) {
   const float2* tw = pfth::twiddles(N);
   if (!tw) return PFT_ERR_CUDA;
-  size_t smem = sizeof(float2) * (N + N * Fft<N>::S);
+  size_t smem = sizeof(float2) * (Fft<N>::TAB + N * Fft<N>::S);
   void* args[] = {(void*)&in, (void*)&out, (void*)&batch, (void*)&inverse, (void*)&tw};
   return launch_persistent(k_fft2<N>, smem, batch, args, st);
 }
@@ -162,7 +166,7 @@ template <int N, int M>
 int run_fft_crop(const void* in, void* out, long long batch, cudaStream_t st) {
   const float2* tw = pfth::twiddles(N);
   if (!tw) return PFT_ERR_CUDA;
-  size_t smem = sizeof(float2) * (N + N * (M + 1) + M * (M + 1));
+  size_t smem = sizeof(float2) * (Fft<N>::TAB + N * (M + 1) + M * (M + 1));
   void* args[] = {(void*)&in, (void*)&out, (void*)&batch, (void*)&tw};
   return launch_persistent(k_fft_crop<N, M>, smem, batch, args, st);
 }

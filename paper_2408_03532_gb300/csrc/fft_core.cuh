@@ -29,28 +29,41 @@ struct Fft {
     return bitrev<E>(f % E) * L + bitrev<L>(f / E);
   }
 
-  // natural order in, slot order out; twN[m] = e^{-2 pi i m / N}
-  __device__ __forceinline__ static void fwd(float2 (&x)[E], int lane, const float2* __restrict__ twN) {
-    reg_dif<E, false>(x, twN, N);
+  // Shared tables of one N: twN[m] = e^{-2 pi i m / N} (N entries, read with
+  // warp-uniform indices), the lane network's stage table (L - 1 entries) and
+  // the twiddles between the two steps, tw2[k1 L + lane] = w_N^{lane k1}.
+  static constexpr int TAB = N + 32 + E * L;
+  __device__ __forceinline__ static void fill(float2* tab, const float2* __restrict__ gtw) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tab[i] = gtw[i];
+    fill_stage_table<L>(tab + N, gtw, N);
+    for (int i = threadIdx.x; i < E * L; i += blockDim.x) tab[N + 32 + i] = gtw[((i % L) * (i / L)) & (N - 1)];
+  }
+
+  using Net = LaneNet<L, false>;
+  __device__ __forceinline__ static void init_net(Net& net, int lane, const float2* __restrict__ tab) {
+    net.init(lane, tab + N);
+  }
+
+  // natural order in, slot order out
+  __device__ __forceinline__ static void fwd(float2 (&x)[E], int lane, const float2* __restrict__ tab,
+                                             const Net& net) {
+    reg_dif<E, false>(x, tab, N);
 #pragma unroll
-    for (int pos = 0; pos < E; ++pos) {
-      const int idx = (lane * bitrev<E>(pos)) & (N - 1);
-      if (idx) x[pos] = cmul(x[pos], twN[idx]);
-    }
+    for (int pos = 0; pos < E; ++pos)
+      if (bitrev<E>(pos)) x[pos] = cmul(x[pos], tab[N + 32 + bitrev<E>(pos) * L + lane]);
 #pragma unroll
-    for (int pos = 0; pos < E; ++pos) x[pos] = lane_dif<L, false, N / L>(x[pos], lane, twN);
+    for (int pos = 0; pos < E; ++pos) x[pos] = net.fwd(x[pos]);
   }
 
   // exact adjoint of fwd: slot order in, natural order out (F^H = N F^{-1})
-  __device__ __forceinline__ static void adj(float2 (&x)[E], int lane, const float2* __restrict__ twN) {
+  __device__ __forceinline__ static void adj(float2 (&x)[E], int lane, const float2* __restrict__ tab,
+                                             const Net& net) {
 #pragma unroll
-    for (int pos = 0; pos < E; ++pos) x[pos] = lane_dif_adj<L, false, N / L>(x[pos], lane, twN);
+    for (int pos = 0; pos < E; ++pos) x[pos] = net.adj(x[pos]);
 #pragma unroll
-    for (int pos = 0; pos < E; ++pos) {
-      const int idx = (lane * bitrev<E>(pos)) & (N - 1);
-      if (idx) x[pos] = cmulc(x[pos], twN[idx]);
-    }
-    reg_dif_adj<E, false>(x, twN, N);
+    for (int pos = 0; pos < E; ++pos)
+      if (bitrev<E>(pos)) x[pos] = cmulc(x[pos], tab[N + 32 + bitrev<E>(pos) * L + lane]);
+    reg_dif_adj<E, false>(x, tab, N);
   }
 };
 

@@ -13,8 +13,8 @@
 //     every index is a compile-time constant, so it is read as a constant
 //     operand of the FMA instructions.
 //   stage B (lines 3-6): a P-point DFT over k for each j, done across the P
-//     lanes by a radix-2 butterfly network with shuffles (lane k then holds
-//     residue v = bitrev(k)), followed by
+//     lanes by a radix-2 butterfly network with shuffles and per-lane register
+//     twiddles (lane k then holds residue v = bitrev(k)), followed by
 //     z^[t] = sum_j W'[t][j] C^[t mod P][j] for the M/P outputs t = v mod P,
 //     where W'[t][j] = i^j (t/P)^j e^{-i pi t/P} carries the factor i^j of
 //     w_j = i^j a_j.
@@ -125,11 +125,11 @@ struct Pft1D {
   __device__ __forceinline__ static void forward(const float2 (&x)[Q], int k,
                                                  const float (&bh)[BH_ROWS][RMAX],
                                                  const float2* __restrict__ sW,
-                                                 const float2* __restrict__ twp, Store store) {
+                                                 const LaneNet<P, false>& net, Store store) {
     float2 C[RMAX];
     stageA_fwd<Q>(x, C, bh);
 #pragma unroll
-    for (int j = 0; j < RMAX; ++j) C[j] = lane_dif<P, false>(C[j], k, twp);
+    for (int j = 0; j < RMAX; ++j) C[j] = net.fwd(C[j]);
     const int w = first_out(k);
 #pragma unroll
     for (int c = 0; c < MP; ++c) {
@@ -147,7 +147,7 @@ struct Pft1D {
   __device__ __forceinline__ static void adjoint(Load load, int k,
                                                  const float (&bh)[BH_ROWS][RMAX],
                                                  const float2* __restrict__ sW,
-                                                 const float2* __restrict__ twp, float2 (&x)[Q]) {
+                                                 const LaneNet<P, false>& net, float2 (&x)[Q]) {
     const int w = first_out(k);
     float2 yv[MP];
 #pragma unroll
@@ -158,7 +158,7 @@ struct Pft1D {
       float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
       for (int c = 0; c < MP; ++c) acc = cfmac(acc, sW[j * M + c * P + w], yv[c]);
-      E[j] = lane_dif_adj<P, false>(acc, k, twp);
+      E[j] = net.adj(acc);
     }
     stageA_adj<Q>(E, x, bh);
   }

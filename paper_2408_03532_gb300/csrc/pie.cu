@@ -135,6 +135,8 @@ struct pie_ctx {
   // kernels per [transform][mode][log2 cluster size] with their resident-CTA capacity
   PieKernel kern[2][3][4];
   long long cap[2][3][4] = {};
+  int tuned[2][3] = {{-1, -1, -1}, {-1, -1, -1}};  // autotuned log2 cluster size, -1 = heuristic
+  double tuned_ms[2] = {0.0, 0.0};                  // sweep time of the chosen variant
   float2* d_probe = nullptr;
   float probe_max2 = 0.f;
   int2* d_pos = nullptr;
@@ -234,12 +236,15 @@ int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) 
   if (a.count <= 0) return PFT_OK;
   const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
   int ci = 0;
-  if (mode == MODE_COLOURED)
+  if (c->tuned[t][mode] >= 0) {
+    ci = c->tuned[t][mode];
+  } else if (mode == MODE_COLOURED) {
     for (int q = 3; q >= 1; --q)
       if (c->kern[t][mode][q].fn && (long long)a.count * (1 << q) <= c->cap[t][mode][q]) {
         ci = q;
         break;
       }
+  }
   const PieKernel& k = c->kern[t][mode][ci];
   if (!k.fn) return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for this transform and mode");
   const long long clusters = std::min<long long>(a.count, std::max<long long>(1, c->cap[t][mode][ci] / k.cluster));
@@ -269,6 +274,53 @@ int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) 
     PFT_CUDA_TRY(cudaLaunchKernelExC(&cfg, k.fn, args));
   }
   return PFT_OK;
+}
+
+int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st);
+
+__global__ void k_fill(float2* __restrict__ z, long long n, float2 v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = v;
+}
+
+// Times one sweep of every built cluster size on a scratch object, for each
+// transform in the context's mode, and keeps the fastest (the autotuner).
+int autotune(pie_ctx* c, cudaStream_t st) {
+  const int mode = c->pb.mode == PIE_MODE_COLOURED ? MODE_COLOURED : MODE_BATCHED;
+  const long long HW = (long long)c->H * c->W;
+  float2* scratch = c->d_prev;
+  cudaEvent_t e0, e1;
+  PFT_CUDA_TRY(cudaEventCreate(&e0));
+  PFT_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = PFT_OK;
+  for (int t = 0; t < 2 && rc == PFT_OK; ++t) {
+    if (t == 1 && !c->have_full) break;
+    const int tr = t == 0 ? PIE_TRANSFORM_PFT : PIE_TRANSFORM_FULL;
+    int best = -1;
+    float best_ms = 1e30f;
+    for (int q = 0; q < 4 && rc == PFT_OK; ++q) {
+      if (!c->kern[t][mode][q].fn) continue;
+      c->tuned[t][mode] = q;
+      k_fill<<<grid_for(HW), kThreads, 0, st>>>(scratch, HW, make_float2(0.7f, 0.2f));
+      rc = enqueue_sweep(c, scratch, tr, 1.0, false, st);  // warm-up
+      if (rc != PFT_OK) break;
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 2 && rc == PFT_OK; ++rep) rc = enqueue_sweep(c, scratch, tr, 1.0, false, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = pfth::set_error(PFT_ERR_CUDA, "autotune sweep failed");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == PFT_OK && ms < best_ms) {
+        best_ms = ms;
+        best = q;
+      }
+    }
+    c->tuned[t][mode] = best;
+    c->tuned_ms[t] = best >= 0 ? best_ms / 2.0 : 0.0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 }  // namespace
@@ -418,9 +470,24 @@ int pie_ctx_create(pie_ctx** out, const pie_problem* pb, const void* probe, cons
                                                     (float)(pb->delta_rel > 0 ? pb->delta_rel : 1e-3), c->d_mask);
   PIE_CUDA(cudaGetLastError());
   PIE_CUDA(cudaStreamSynchronize(st));
+  if (pb->autotune) PIE_TRY(autotune(c, st));
 #undef PIE_TRY
 #undef PIE_CUDA
   *out = c;
+  return PFT_OK;
+}
+
+int pie_ctx_info_get(const pie_ctx* c, pie_ctx_info* info) {
+  if (!c || !info) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  const int mode = c->pb.mode == PIE_MODE_COLOURED ? MODE_COLOURED : MODE_BATCHED;
+  info->ncolours = c->ncol;
+  info->p = c->plan.p1;
+  info->q = c->plan.q1;
+  info->r = c->plan.r1;
+  info->cluster_pft = c->tuned[0][mode] >= 0 ? (1 << c->tuned[0][mode]) : 0;
+  info->cluster_full = c->tuned[1][mode] >= 0 ? (1 << c->tuned[1][mode]) : 0;
+  info->sweep_ms_pft = c->tuned_ms[0];
+  info->sweep_ms_full = c->tuned_ms[1];
   return PFT_OK;
 }
 

@@ -33,6 +33,8 @@ void add_size(std::vector<Entry>& v) {
   add<N, MODE_COLOURED, 4>(v);
   add<N, MODE_COLOURED, 8>(v);
   add<N, MODE_BATCHED, 1>(v);
+  add<N, MODE_BATCHED, 2>(v);
+  add<N, MODE_BATCHED, 4>(v);
 }
 
 std::vector<Entry> build_table() {

@@ -126,7 +126,7 @@ struct PiePftShape {
   static constexpr int OFF_W1 = 0;
   static constexpr int OFF_W2 = OFF_W1 + RMAX * M;
   static constexpr int OFF_TW = OFF_W2 + RMAX * M;
-  static constexpr int OFF_Y = OFF_TW + 16;
+  static constexpr int OFF_Y = OFF_TW + 32;
   static constexpr int Y_SIZE = CM * SYT;
   static constexpr int G_SIZE = RN * SG;
   static constexpr int OFF_G = (C == 1) ? OFF_Y : OFF_Y + Y_SIZE;  // alias for one CTA
@@ -151,12 +151,14 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
   float2* sZ = sm + S::OFF_Z;
   double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
   for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) sm[i] = gW[i];
-  for (int i = threadIdx.x; i < P / 2; i += NT) stw[i] = gtw[i];
+  fill_stage_table<P>(stw, gtw, P);
   const unsigned rank = CL::rank();
   CL::sync();  // every CTA of the cluster has started before any remote store
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = lane % P, g = lane / P;
   const int r0 = rank * RN;
+  LaneNet<P, false> net;
+  net.init(k, stw);
   for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
     const int j = a.list ? a.list[it] : it;
     const int2 rc = a.pos[j];
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
         const int v = Q * k + l;
         xv[l] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
       }
-      T::forward(xv, k, c.bh[1], sW2, stw, [&](int t, float2 val) {
+      T::forward(xv, k, c.bh[1], sW2, net, [&](int t, float2 val) {
         float2* dst = CL::map(sY, (unsigned)(t / CM));
         dst[(t % CM) * S::SYT + u + u / Q] = val;
       });
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
       float2 xv[Q];
 #pragma unroll
       for (int l = 0; l < Q; ++l) xv[l] = sY[tl * S::SYT + Q * k + l + k];
-      T::forward(xv, k, c.bh[0], sW1, stw, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
+      T::forward(xv, k, c.bh[0], sW1, net, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
     }
     __syncthreads();
     // 3b. modulus projection on the M x CM coefficients
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
     for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
       const int tl = cs0 + g;
       float2 xv[Q];
-      T::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, c.bh[0], sW1, stw, xv);
+      T::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, c.bh[0], sW1, net, xv);
       const int u0 = Q * k;
       float2* dst = CL::map(sG, (unsigned)(u0 / RN));
       const int tg = rank * CM + tl;
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int ul = u0 + g, u = r0 + ul;
       float2 xv[Q];
-      T::adjoint([&](int t) { return sG[ul * S::SG + t]; }, k, c.bh[1], sW2, stw, xv);
+      T::adjoint([&](int t) { return sG[ul * S::SG + t]; }, k, c.bh[1], sW2, net, xv);
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
         const int v = Q * k + l;
@@ -230,7 +232,7 @@ struct PieFullShape {
   static constexpr int SCS = CN + 1;  // column slice: [N][CN + 1]
   static constexpr int SRS = N + 1;   // row slice: [RN][N + 1]
   static constexpr int OFF_TW = 0;
-  static constexpr int OFF_C = N;
+  static constexpr int OFF_C = F::TAB;
   static constexpr int OFF_R = (C == 1) ? OFF_C : OFF_C + N * SCS;  // alias for one CTA
   static constexpr int OFF_RED = (C == 1) ? OFF_C + N * SCS : OFF_R + RN * SRS;
   static constexpr size_t SMEM = sizeof(float2) * (OFF_RED + 16);
@@ -247,12 +249,14 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
   float2* sC = sm + S::OFF_C;
   float2* sR = sm + S::OFF_R;
   double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
-  for (int i = threadIdx.x; i < N; i += NT) tw[i] = gtw[i];
+  F::fill(tw, gtw);
   const unsigned rank = CL::rank();
   CL::sync();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l = lane % L, g = lane / L;
   const int r0 = rank * RN, c0 = rank * CN;
+  typename F::Net net;
+  F::init_net(net, l, tw);
   for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
     const int j = a.list ? a.list[it] : it;
     const int2 rc = a.pos[j];
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
         const int v = l + L * e;
         x[e] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
       }
-      F::fwd(x, l, tw);
+      F::fwd(x, l, tw, net);
 #pragma unroll
       for (int p = 0; p < E; ++p) {
         const int s = p * L + l;
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
       float2 x[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) x[e] = sC[(l + L * e) * S::SCS + b];
-      F::fwd(x, l, tw);
+      F::fwd(x, l, tw, net);
 #pragma unroll
       for (int p = 0; p < E; ++p) sC[(p * L + l) * S::SCS + b] = x[p];
     }
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
       float2 x[E];
 #pragma unroll
       for (int p = 0; p < E; ++p) x[p] = sC[(p * L + l) * S::SCS + b];
-      F::adj(x, l, tw);
+      F::adj(x, l, tw, net);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int u = l + L * e;
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
       float2 x[E];
 #pragma unroll
       for (int p = 0; p < E; ++p) x[p] = sR[ul * S::SRS + p * L + l];
-      F::adj(x, l, tw);
+      F::adj(x, l, tw, net);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int v = l + L * e;

@@ -33,6 +33,8 @@ void add_shape(std::vector<Entry>& v) {
   add<P, Q, MP, MODE_COLOURED, 4>(v);
   add<P, Q, MP, MODE_COLOURED, 8>(v);
   add<P, Q, MP, MODE_BATCHED, 1>(v);
+  add<P, Q, MP, MODE_BATCHED, 2>(v);
+  add<P, Q, MP, MODE_BATCHED, 4>(v);
   add<P, Q, MP, MODE_GRAD, 1>(v);
 }
 

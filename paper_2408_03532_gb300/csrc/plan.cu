@@ -59,7 +59,7 @@ struct FrameShape {
   static constexpr int OFF_W1 = 0;
   static constexpr int OFF_W2 = OFF_W1 + RMAX * M;
   static constexpr int OFF_TW = OFF_W2 + RMAX * M;
-  static constexpr int OFF_Y = OFF_TW + 16;
+  static constexpr int OFF_Y = OFF_TW + 32;
   static constexpr int OFF_Z = OFF_Y + N * L::S;
   static constexpr int ZS = M + 1;
   static constexpr int FLOATS2 = OFF_Z + M * ZS;
@@ -84,10 +84,11 @@ __device__ __forceinline__ void store_block_v4(float2* dst, const float2 (&x)[Q]
   for (int i = 0; i < Q / 2; ++i) d4[i] = make_float4(x[2 * i].x, x[2 * i].y, x[2 * i + 1].x, x[2 * i + 1].y);
 }
 
+template <int P>
 __device__ __forceinline__ void load_tables(float2* sm, const float2* __restrict__ gW, const float2* __restrict__ gtw,
-                                            int nW, int off_tw, int p) {
+                                            int nW, int off_tw) {
   for (int i = threadIdx.x; i < nW; i += blockDim.x) sm[i] = gW[i];
-  for (int i = threadIdx.x; i < p / 2; i += blockDim.x) sm[off_tw + i] = gtw[i];
+  fill_stage_table<P>(sm + off_tw, gtw, P);
 }
 
 // y[f] = A1 x[f] A2^T  (Algorithm 5), one frame per CTA iteration.
@@ -104,18 +105,34 @@ __global__ void __launch_bounds__(kThreads) k_pft_fwd(const float2* __restrict__
   float2* stw = sm + S::OFF_TW;
   float2* sY = sm + S::OFF_Y;
   float2* sZ = sm + S::OFF_Z;
-  load_tables(sm, gW, gtw, 2 * RMAX * M, S::OFF_TW, P);
+  load_tables<P>(sm, gW, gtw, 2 * RMAX * M, S::OFF_TW);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = lane % P, g = lane / P;
+  LaneNet<P, false> net;
+  net.init(k, stw);
+  // Each warp keeps the next row block's loads in flight while it computes the
+  // current one (also across frames, so they overlap the column pass).
+  constexpr int STEP = kWarps * G;
+  float2 xn[Q];
+  long long fn = blockIdx.x;
+  int un = warp * G;
+  if (fn < batch) load_block_v4<Q>(x + fn * (long long)(N * N) + (un + g) * N + Q * k, xn);
   for (long long f = blockIdx.x; f < batch; f += gridDim.x) {
-    const float2* xf = x + f * (long long)(N * N);
     // rows: axis 2
-    for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
+    for (int u0 = warp * G; u0 < N; u0 += STEP) {
       const int u = u0 + g;
       float2 xv[Q];
-      load_block_v4<Q>(xf + u * N + Q * k, xv);
-      T::forward(xv, k, c.bh[1], sW2, stw, [&](int t, float2 v) { sY[S::L::at(u, t)] = v; });
+#pragma unroll
+      for (int l = 0; l < Q; ++l) xv[l] = xn[l];
+      un = u0 + STEP;
+      fn = f;
+      if (un >= N) {
+        un = warp * G;
+        fn = f + gridDim.x;
+      }
+      if (fn < batch) load_block_v4<Q>(x + fn * (long long)(N * N) + (un + g) * N + Q * k, xn);
+      T::forward(xv, k, c.bh[1], sW2, net, [&](int t, float2 v) { sY[S::L::at(u, t)] = v; });
     }
     __syncthreads();
     // columns: axis 1
@@ -124,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_pft_fwd(const float2* __restrict__
       float2 xv[Q];
 #pragma unroll
       for (int l = 0; l < Q; ++l) xv[l] = sY[S::L::at(Q * k + l, t2)];
-      T::forward(xv, k, c.bh[0], sW1, stw, [&](int t1, float2 v) { sZ[t1 * S::ZS + t2] = v; });
+      T::forward(xv, k, c.bh[0], sW1, net, [&](int t1, float2 v) { sZ[t1 * S::ZS + t2] = v; });
     }
     __syncthreads();
     float2* yf = y + f * (long long)(M * M);
@@ -147,10 +164,12 @@ __global__ void __launch_bounds__(kThreads) k_pft_adj(const float2* __restrict__
   float2* stw = sm + S::OFF_TW;
   float2* sY = sm + S::OFF_Y;
   float2* sZ = sm + S::OFF_Z;
-  load_tables(sm, gW, gtw, 2 * RMAX * M, S::OFF_TW, P);
+  load_tables<P>(sm, gW, gtw, 2 * RMAX * M, S::OFF_TW);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = lane % P, g = lane / P;
+  LaneNet<P, false> net;
+  net.init(k, stw);
   for (long long f = blockIdx.x; f < batch; f += gridDim.x) {
     const float2* yf = y + f * (long long)(M * M);
     for (int i = threadIdx.x; i < M * M; i += kThreads) sZ[(i / M) * S::ZS + (i % M)] = __ldg(yf + i);
@@ -159,7 +178,7 @@ __global__ void __launch_bounds__(kThreads) k_pft_adj(const float2* __restrict__
     for (int cs0 = warp * G; cs0 < M; cs0 += kWarps * G) {
       const int t2 = col_of<P>(cs0 + g);
       float2 xv[Q];
-      T::adjoint([&](int t1) { return sZ[t1 * S::ZS + t2]; }, k, c.bh[0], sW1, stw, xv);
+      T::adjoint([&](int t1) { return sZ[t1 * S::ZS + t2]; }, k, c.bh[0], sW1, net, xv);
 #pragma unroll
       for (int l = 0; l < Q; ++l) sY[S::L::at(Q * k + l, t2)] = xv[l];
     }
@@ -169,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_pft_adj(const float2* __restrict__
     for (int u0 = warp * G; u0 < N; u0 += kWarps * G) {
       const int u = u0 + g;
       float2 xv[Q];
-      T::adjoint([&](int t) { return sY[S::L::at(u, t)]; }, k, c.bh[1], sW2, stw, xv);
+      T::adjoint([&](int t) { return sY[S::L::at(u, t)]; }, k, c.bh[1], sW2, net, xv);
       store_block_v4<Q>(xf + u * N + Q * k, xv);
     }
     __syncthreads();

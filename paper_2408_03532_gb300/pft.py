@@ -41,7 +41,13 @@ class PlanInfo(ctypes.Structure):
 class PieProblem(ctypes.Structure):
     _fields_ = [("obj_h", ctypes.c_int), ("obj_w", ctypes.c_int), ("n", ctypes.c_int), ("npos", ctypes.c_int),
                 ("M", ctypes.c_int), ("p", ctypes.c_int), ("eps", ctypes.c_double), ("mode", ctypes.c_int),
-                ("path", ctypes.c_int), ("delta_rel", ctypes.c_double)]
+                ("path", ctypes.c_int), ("delta_rel", ctypes.c_double), ("autotune", ctypes.c_int)]
+
+
+class PieCtxInfo(ctypes.Structure):
+    _fields_ = [("ncolours", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int), ("r", ctypes.c_int),
+                ("cluster_pft", ctypes.c_int), ("cluster_full", ctypes.c_int),
+                ("sweep_ms_pft", ctypes.c_double), ("sweep_ms_full", ctypes.c_double)]
 
 
 class PieStats(ctypes.Structure):
@@ -94,6 +100,7 @@ def load() -> ctypes.CDLL:
         "pie_ctx_create": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
         "pie_ctx_destroy": (ctypes.c_int, [_P]),
         "pie_ctx_colours": (ctypes.c_int, [_P, _P, _P]),
+        "pie_ctx_info_get": (ctypes.c_int, [_P, _P]),
         "pie_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
         "warm_start_then_refine": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -264,19 +271,25 @@ class PieContext:
     """One ptychography problem resident on the GPU (probe, scan, amplitudes, plans)."""
 
     def __init__(self, obj_shape, probe, positions, intensities, M: int, p: int = 0, eps: float = 1e-7,
-                 mode: int = MODE_COLOURED, delta_rel: float = 1e-3, stream=None):
+                 mode: int = MODE_COLOURED, delta_rel: float = 1e-3, autotune: bool = True, stream=None):
         import torch
         n = probe.shape[-1]
         _need(probe, torch.complex64, (n, n), "probe")
         _need(intensities, torch.float32, (n, n), "intensities")
         pos = np.ascontiguousarray(np.asarray(positions, dtype=np.int32).reshape(-1, 2))
-        prob = PieProblem(int(obj_shape[0]), int(obj_shape[1]), n, len(pos), M, p, eps, mode, PATH_AUTO, delta_rel)
+        prob = PieProblem(int(obj_shape[0]), int(obj_shape[1]), n, len(pos), M, p, eps, mode, PATH_AUTO, delta_rel,
+                          int(autotune))
         h = ctypes.c_void_p()
         _check(load().pie_ctx_create(ctypes.byref(h), ctypes.byref(prob), _ptr(probe), pos.ctypes.data,
                                      _ptr(intensities), _stream(stream)))
         self._h = h
         self.shape = (int(obj_shape[0]), int(obj_shape[1]))
         self.n, self.M, self.npos = n, M, len(pos)
+
+    def info(self) -> dict:
+        i = PieCtxInfo()
+        _check(load().pie_ctx_info_get(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in PieCtxInfo._fields_}
 
     def colours(self) -> np.ndarray:
         nc = ctypes.c_int()

@@ -217,3 +217,39 @@ def test_errors(env, small):
     with pytest.raises(pft.PftError):
         pft.PieContext(P["obj"].shape, c64(P["probe"], torch), P["pos"],
                        torch.from_numpy(P["intensities"].astype(np.float32)).cuda(), M=15)
+
+
+def test_autograd_function_matches_oracle_and_fd(env):
+    """The autograd.Function over the gradient kernel (512^2 / 64^2 / 400
+    positions): loss.backward() gives the oracle's gradients for object and
+    probe, and the object gradient agrees with FP64 central differences
+    (h = 1e-6) of the oracle's loss on 50 random entries."""
+    torch, pft = env
+    from paper_2408_03532_gb300.autograd import amplitude_loss
+    G = synth.gradient_problem()
+    ctx = make_ctx(G, torch, pft)
+    z = c64(G["init"], torch).requires_grad_(True)
+    w = c64(G["probe"], torch).requires_grad_(True)
+    loss = amplitude_loss(z, w, ctx)
+    (2.0 * loss).backward()
+    gz = z.grad.cpu().numpy() / 2.0
+    gw = w.grad.cpu().numpy() / 2.0
+    P1, P2 = coeffs.plan_2d(64, 64, 32, 32, 16, 16)
+    T = opie.pft_transform(P1, P2)
+    d = opie.amplitudes(G["intensities"], 32).astype(np.float32).astype(np.float64)
+    z64 = G["init"].astype(np.complex64).astype(np.complex128)
+    w64 = G["probe"].astype(np.complex64).astype(np.complex128)
+    lo, gzo, gwo = ograd.amplitude_loss_grad(z64, w64, G["pos"], d, T)
+    assert float(loss) == pytest.approx(lo, rel=TOL)
+    assert rel(gz, gzo) < TOL and rel(gw, gwo) < TOL
+    rng = np.random.default_rng(5)
+    pos = G["pos"]
+    il = opie.illumination(G["probe"], pos, z64.shape)
+    cand = np.argwhere(il > 1e-2 * il.max())
+    scale = np.abs(gzo).max()
+    for k in rng.choice(len(cand), 50, replace=False):
+        r, c = cand[k]
+        cover = [j for j, (a, b) in enumerate(pos) if a <= r < a + 64 and b <= c < b + 64]
+        fd = ograd.finite_difference(lambda zz: ograd.amplitude_loss(zz, w64, pos[cover], d[cover], T),
+                                     z64, (r, c), 1e-6)
+        assert abs(gz[r, c] - fd) <= 1e-5 * scale
