@@ -236,6 +236,7 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-pft-batch", action="store_true")
     ap.add_argument("--pft-frames", type=int, default=4096)
+    ap.add_argument("--no-batch64", action="store_true")
     args = ap.parse_args()
     rank, world, local = dist_env()
 
@@ -341,6 +342,7 @@ def main() -> None:
         ttt = time_to_target(ctx, pft, torch, init, truth, args, stream)
 
     pft_batch = None if args.no_pft_batch else measure_pft_batch(pft, torch, dev, stream, flush, args.pft_frames)
+    batch64 = None if args.no_batch64 else measure_batch64(pft, synth, torch, dev, stream, flush)
 
     # roofline of the dominant kernel (per sweep of launches of that kernel)
     pinfo = pft.Plan(n, M).info
@@ -372,7 +374,7 @@ def main() -> None:
                         "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                 "gpu_launches": 2 * launches_per_sweep * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "time_to_target": ttt, "pft_batch": pft_batch, "wall_s": wall, "colours": ncol,
+                "time_to_target": ttt, "pft_batch": pft_batch, "batch64": batch64, "wall_s": wall, "colours": ncol,
                 "autotune": tuning}
         print(json.dumps(line))
     if world > 1:
@@ -424,6 +426,44 @@ def measure_pft_batch(pft, torch, dev, stream, flush, frames: int = 4096, n: int
                         "frames_per_s_forward": frames / (f / 1e3)}
         del y, xa, plan
     del x
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_batch64(pft, synth, torch, dev, stream, flush, reps: int = 3) -> dict:
+    """64 independent reconstructions of different sizes (objects 256^2-2048^2,
+    probes 64^2-256^2, 50-2000 Fermat positions, M in {16, 32, 64}) swept
+    together: one PFT sweep over all instances per graph launch, coloured
+    (exact PIE order) and batched modes, timed with CUDA events."""
+    specs = synth.uneven_batch_recipe(64)
+    insts, inits = [], []
+    for sp in specs:
+        inst = synth.make_instance(sp)
+        obj = torch.from_numpy(inst["obj"].astype(np.complex64)).to(dev)
+        pr = torch.from_numpy(inst["probe"].astype(np.complex64)).to(dev)
+        insts.append(dict(obj_shape=inst["obj"].shape, probe=pr, positions=inst["pos"],
+                          intensities=synth.simulate_intensities_torch(obj, pr, inst["pos"]), M=sp["M"]))
+        inits.append(torch.from_numpy(inst["init"].astype(np.complex64)).to(dev))
+    frames = sum(sp["npos"] for sp in specs)
+    out = {"instances": len(specs), "positions": frames}
+    for name, mode in (("coloured", pft.MODE_COLOURED), ("batched", pft.MODE_BATCHED)):
+        B = pft.PieBatch(insts, mode=mode)
+        objs = [z.clone() for z in inits]
+        B.iteration(objs, pft.TRANSFORM_PFT, 1.0, stats=False)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            B.iteration(objs, pft.TRANSFORM_PFT, 1.0, stats=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        nclass, nlaunch = B.classes()
+        out[name] = {"pft_sweep_ms": statistics.median(ms), "frames_per_s": frames / (statistics.median(ms) / 1e3),
+                     "shape_classes": nclass, "launches_per_sweep": nlaunch}
+        B.close()
+    del insts
     torch.cuda.empty_cache()
     return out
 

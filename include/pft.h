@@ -248,6 +248,34 @@ int pie_nrmse(pie_ctx* ctx, const void* object, const void* truth, double* out, 
 int pie_amp_loss_grad(pie_ctx* ctx, const void* object, const void* probe, void* grad_obj,
                       void* grad_probe, double* loss, void* stream);
 
+/* ---- many independent reconstructions ------------------------------------
+ * A batch holds `count` independent PIE problems whose sizes may differ (the
+ * object, probe, scan and output size of each instance are its own). One call
+ * sweeps every position of every instance: instances with the same (n, M) form
+ * a shape class whose positions share one kernel launch per colour (coloured
+ * mode: launch c runs colour c of all of them) or one launch per sweep
+ * (batched mode); the classes run as parallel branches of one CUDA graph,
+ * captured on first use and replayed.
+ *
+ * pie_batch_create(out, count, problems, probes, positions, intensities, stream)
+ *   problems: host [count] (all with the same mode; `autotune` is ignored);
+ *   probes, positions, intensities: host arrays of `count` pointers, each as
+ *   for pie_ctx_create. Synchronises `stream`.
+ * pie_batch_iteration(b, objects, transform, beta, phi, stream)
+ *   objects: host array of `count` device object pointers (updated in place);
+ *   phi: host double [count] or NULL; with it the call synchronises and
+ *   writes each instance's Phi (as pie_stats.phi).
+ * pie_batch_classes: number of shape classes and kernel launches per sweep.
+ */
+typedef struct pie_batch pie_batch;
+
+int pie_batch_create(pie_batch** out, int count, const pie_problem* problems, const void* const* probes,
+                     const int32_t* const* positions, const float* const* intensities, void* stream);
+int pie_batch_destroy(pie_batch* batch);
+int pie_batch_iteration(pie_batch* batch, void* const* objects, int transform, double beta, double* phi,
+                        void* stream);
+int pie_batch_classes(const pie_batch* batch, int* nclasses, int* launches_per_sweep);
+
 /* ---- allocation-free error reduction ------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot
  * allocate device memory when they need the error: code being recorded into a

@@ -512,6 +512,8 @@ int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stat
   PFT_CUDA_TRY(cudaMemsetAsync(c->d_red, 0, sizeof(double) * 8, st));
   const float n2 = (float)c->n * (float)c->n;
   PieArgs a;
+  a.inst = nullptr;
+  a.work = nullptr;
   a.obj = obj;
   a.objr = obj;
   a.obj_w = c->W;
@@ -664,6 +666,8 @@ int pie_amp_loss_grad(pie_ctx* c, const void* object, const void* probe, void* g
   if (grad_probe) PFT_CUDA_TRY(cudaMemsetAsync(grad_probe, 0, sizeof(float2) * c->n * c->n, st));
   PFT_CUDA_TRY(cudaMemsetAsync(c->d_red, 0, sizeof(double), st));
   PieArgs a;
+  a.inst = nullptr;
+  a.work = nullptr;
   a.obj = nullptr;
   a.objr = (const float2*)object;
   a.obj_w = c->W;
@@ -682,6 +686,275 @@ int pie_amp_loss_grad(pie_ctx* c, const void* object, const void* probe, void* g
   PFT_CUDA_TRY(cudaStreamSynchronize(st));
   *loss = c->h_red[0];
   if (!std::isfinite(*loss)) return pfth::set_error(PFT_ERR_NONFINITE, "non-finite loss");
+  return PFT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------
+// Many independent reconstructions swept together.
+// ------------------------------------------------------------------------
+struct pie_batch {
+  int count = 0;
+  int mode = PIE_MODE_COLOURED;
+  std::vector<pie_ctx*> ctx;
+  struct Class {
+    int rep = 0;                    // member whose kernels and tables the class uses
+    std::vector<int> members;
+    std::vector<int> col_off;       // work-list offsets per colour (coloured mode)
+    int2* d_work = nullptr;         // (instance, position) pairs, colour-major
+    bool have_full = true;
+  };
+  std::vector<Class> classes;
+  std::vector<PieInstance> h_inst;
+  double* d_red = nullptr;
+  double* h_red = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> events;  // [0] fork, [1 + k] join of class k
+  struct Graph {
+    std::vector<void*> objs;
+    int transform;
+    double beta;
+    bool stats;
+    cudaGraphExec_t exec;
+    PieInstance* d_inst;  // the instance descriptors this graph reads
+  };
+  std::vector<Graph> graphs;
+};
+
+namespace {
+
+// Instance descriptors for these objects and this step size (host side).
+void batch_descriptors(pie_batch* b, void* const* objects, int transform, double beta) {
+  const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
+  const bool coloured = b->mode == PIE_MODE_COLOURED;
+  b->h_inst.resize(b->count);
+  for (int i = 0; i < b->count; ++i) {
+    pie_ctx* c = b->ctx[i];
+    PieInstance& in = b->h_inst[i];
+    const double n2 = (double)c->n * (double)c->n;
+    in.obj = (float2*)objects[i];
+    in.obj_w = c->W;
+    in.probe = c->d_probe;
+    in.pos = c->d_pos;
+    in.dat = t == 0 ? c->d_ampc : c->d_amp;
+    in.coef = coloured ? (float)(beta / ((double)c->probe_max2 * n2)) : (float)(1.0 / n2);
+    in.acc = c->d_acc;
+    in.red = b->d_red + i;
+  }
+}
+
+int batch_enqueue(pie_batch* b, const PieInstance* d_inst, void* const* objects, int transform, double beta,
+                  bool stats, cudaStream_t st) {
+  const int mode = b->mode == PIE_MODE_COLOURED ? MODE_COLOURED : MODE_BATCHED;
+  PFT_CUDA_TRY(cudaMemsetAsync(b->d_red, 0, sizeof(double) * b->count, st));
+  if (mode == MODE_BATCHED)
+    for (pie_ctx* c : b->ctx)
+      PFT_CUDA_TRY(cudaMemsetAsync(c->d_acc, 0, sizeof(float2) * (size_t)c->H * c->W, st));
+  PFT_CUDA_TRY(cudaEventRecord(b->events[0], st));
+  for (size_t k = 0; k < b->classes.size(); ++k) {
+    const pie_batch::Class& cl = b->classes[k];
+    cudaStream_t bs = b->branch[k];
+    PFT_CUDA_TRY(cudaStreamWaitEvent(bs, b->events[0], 0));
+    PieArgs a = {};
+    a.inst = d_inst;
+    const int ncol = mode == MODE_COLOURED ? (int)cl.col_off.size() - 1 : 1;
+    for (int col = 0; col < ncol; ++col) {
+      const int off = mode == MODE_COLOURED ? cl.col_off[col] : 0;
+      a.work = cl.d_work + off;
+      a.count = mode == MODE_COLOURED ? cl.col_off[col + 1] - off : cl.col_off.back();
+      int rc = launch_pie(b->ctx[cl.rep], transform, mode, a, bs);
+      if (rc != PFT_OK) return rc;
+    }
+    PFT_CUDA_TRY(cudaEventRecord(b->events[1 + k], bs));
+    PFT_CUDA_TRY(cudaStreamWaitEvent(st, b->events[1 + k], 0));
+  }
+  if (mode == MODE_BATCHED)
+    for (int i = 0; i < b->count; ++i) {
+      pie_ctx* c = b->ctx[i];
+      const long long HW = (long long)c->H * c->W;
+      k_apply_batched<<<grid_for(HW), kThreads, 0, st>>>((float2*)objects[i], c->d_acc, c->d_inv_illum,
+                                                         (float)beta, HW);
+      PFT_CUDA_TRY(cudaGetLastError());
+    }
+  if (stats)
+    PFT_CUDA_TRY(cudaMemcpyAsync(b->h_red, b->d_red, sizeof(double) * b->count, cudaMemcpyDeviceToHost, st));
+  return PFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pie_batch_destroy(pie_batch* b) {
+  if (!b) return PFT_OK;
+  for (auto& g : b->graphs) {
+    cudaGraphExecDestroy(g.exec);
+    cudaFree(g.d_inst);
+  }
+  for (auto& cl : b->classes) cudaFree(cl.d_work);
+  for (auto* c : b->ctx) pie_ctx_destroy(c);
+  cudaFree(b->d_red);
+  if (b->h_red) cudaFreeHost(b->h_red);
+  for (auto s : b->branch) cudaStreamDestroy(s);
+  for (auto e : b->events) cudaEventDestroy(e);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+  return PFT_OK;
+}
+
+int pie_batch_create(pie_batch** out, int count, const pie_problem* problems, const void* const* probes,
+                     const int32_t* const* positions, const float* const* intensities, void* stream) {
+  if (!out || !problems || !probes || !positions || !intensities || count <= 0)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument or count <= 0");
+  *out = nullptr;
+  for (int i = 1; i < count; ++i)
+    if (problems[i].mode != problems[0].mode)
+      return pfth::set_error(PFT_ERR_INVALID_ARG, "all instances of a batch use the same mode");
+  pie_batch* b = new (std::nothrow) pie_batch();
+  if (!b) return pfth::set_error(PFT_ERR_OOM, "host allocation failed");
+  b->count = count;
+  b->mode = problems[0].mode;
+  int rc = PFT_OK;
+  for (int i = 0; i < count && rc == PFT_OK; ++i) {
+    pie_problem pb = problems[i];
+    pb.autotune = 0;  // the batch picks cluster sizes per launch
+    pie_ctx* c = nullptr;
+    rc = pie_ctx_create(&c, &pb, probes[i], positions[i], intensities[i], stream);
+    if (rc == PFT_OK) b->ctx.push_back(c);
+  }
+  if (rc != PFT_OK) {
+    pie_batch_destroy(b);
+    return rc;
+  }
+  // shape classes: instances whose kernels and tables coincide
+  for (int i = 0; i < count; ++i) {
+    pie_ctx* c = b->ctx[i];
+    int k = -1;
+    for (size_t q = 0; q < b->classes.size(); ++q) {
+      pie_ctx* r = b->ctx[b->classes[q].rep];
+      if (r->n == c->n && r->M == c->M && r->plan.p1 == c->plan.p1 && r->plan.r1 == c->plan.r1 &&
+          r->plan.xi1 == c->plan.xi1)
+        k = (int)q;
+    }
+    if (k < 0) {
+      b->classes.push_back(pie_batch::Class());
+      k = (int)b->classes.size() - 1;
+      b->classes[k].rep = i;
+    }
+    b->classes[k].members.push_back(i);
+    b->classes[k].have_full = b->classes[k].have_full && c->have_full;
+  }
+  auto fail = [&](cudaError_t e, const char* what) {
+    int code = pfth::cuda_error(e, what);
+    pie_batch_destroy(b);
+    return code;
+  };
+  for (auto& cl : b->classes) {
+    int ncol = 0;
+    for (int i : cl.members) ncol = std::max(ncol, b->mode == PIE_MODE_COLOURED ? b->ctx[i]->ncol : 1);
+    std::vector<int2> work;
+    cl.col_off.assign(1, 0);
+    for (int col = 0; col < ncol; ++col) {
+      for (int i : cl.members) {
+        pie_ctx* c = b->ctx[i];
+        for (int j = 0; j < c->npos; ++j)
+          if (b->mode != PIE_MODE_COLOURED || c->colour[j] == col) work.push_back(make_int2(i, j));
+      }
+      cl.col_off.push_back((int)work.size());
+    }
+    cudaError_t e = cudaMalloc(&cl.d_work, sizeof(int2) * work.size());
+    if (e != cudaSuccess) return fail(e, "cudaMalloc(work)");
+    e = cudaMemcpy(cl.d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(e, "cudaMemcpy(work)");
+  }
+  cudaError_t e = cudaMalloc(&b->d_red, sizeof(double) * count);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_red, sizeof(double) * count);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  for (size_t k = 0; k < b->classes.size() && e == cudaSuccess; ++k) {
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->branch.push_back(s);
+  }
+  for (size_t k = 0; k <= b->classes.size() && e == cudaSuccess; ++k) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->events.push_back(ev);
+  }
+  if (e != cudaSuccess) return fail(e, "batch resources");
+  *out = b;
+  return PFT_OK;
+}
+
+int pie_batch_iteration(pie_batch* b, void* const* objects, int transform, double beta, double* phi,
+                        void* stream) {
+  if (!b || !objects) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
+  for (int i = 0; i < b->count; ++i)
+    if (!objects[i]) return pfth::set_error(PFT_ERR_INVALID_ARG, "object %d is NULL", i);
+  if (transform == PIE_TRANSFORM_FULL)
+    for (auto& cl : b->classes)
+      if (!cl.have_full)
+        return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n <= 128, not %d",
+                               b->ctx[cl.rep]->n);
+  std::vector<void*> objs(objects, objects + b->count);
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : b->graphs)
+    if (g.objs == objs && g.transform == transform && g.beta == beta && g.stats == (phi != nullptr))
+      exec = g.exec;
+  if (!exec) {
+    batch_descriptors(b, objects, transform, beta);
+    PieInstance* d_inst = nullptr;
+    PFT_CUDA_TRY(cudaMalloc(&d_inst, sizeof(PieInstance) * b->count));
+    cudaError_t e = cudaMemcpy(d_inst, b->h_inst.data(), sizeof(PieInstance) * b->count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d_inst);
+      return pfth::cuda_error(e, "cudaMemcpy(instances)");
+    }
+    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaFree(d_inst);
+      return pfth::cuda_error(e, "cudaStreamBeginCapture");
+    }
+    int rc = batch_enqueue(b, d_inst, objects, transform, beta, phi != nullptr, b->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (rc == PFT_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != PFT_OK || e != cudaSuccess) {
+      cudaFree(d_inst);
+      return rc != PFT_OK ? rc : pfth::cuda_error(e, "sweep graph capture");
+    }
+    if (b->graphs.size() >= 8) {
+      cudaGraphExecDestroy(b->graphs.front().exec);
+      cudaFree(b->graphs.front().d_inst);
+      b->graphs.erase(b->graphs.begin());
+    }
+    b->graphs.push_back({objs, transform, beta, phi != nullptr, exec, d_inst});
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  PFT_CUDA_TRY(cudaGraphLaunch(exec, st));
+  if (phi) {
+    PFT_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < b->count; ++i) {
+      pie_ctx* c = b->ctx[i];
+      phi[i] = b->h_red[i] / ((double)c->npos * (double)c->n * (double)c->n);
+      if (!std::isfinite(phi[i])) return pfth::set_error(PFT_ERR_NONFINITE, "non-finite objective (instance %d)", i);
+    }
+  }
+  return PFT_OK;
+}
+
+int pie_batch_classes(const pie_batch* b, int* nclasses, int* launches_per_sweep) {
+  if (!b || !nclasses) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  *nclasses = (int)b->classes.size();
+  if (launches_per_sweep) {
+    int l = 0;
+    for (auto& cl : b->classes) l += (int)cl.col_off.size() - 1;
+    *launches_per_sweep = l;
+  }
   return PFT_OK;
 }
 

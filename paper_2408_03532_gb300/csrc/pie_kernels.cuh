@@ -29,7 +29,23 @@ namespace cg = cooperative_groups;
 
 enum { MODE_COLOURED = 0, MODE_BATCHED = 1, MODE_GRAD = 2 };
 
+// One instance of a multi-instance sweep (every pointer is that instance's).
+struct PieInstance {
+  float2* obj;
+  long long obj_w;
+  const float2* probe;
+  const int2* pos;
+  const float* dat;
+  float coef;
+  float2* acc;
+  double* red;
+};
+
 struct PieArgs {
+  // multi-instance sweeps: work item it is (instance, position) = work[it];
+  // when inst == nullptr the single-instance fields below are used
+  const PieInstance* inst;
+  const int2* work;
   float2* obj;              // object [H][W] (written in MODE_COLOURED)
   const float2* objr;       // object read pointer (= obj, or the gradient's input)
   long long obj_w;
@@ -88,19 +104,66 @@ __device__ __forceinline__ float2 residual(float2 Psi, float d, double& acc) {
   return R;
 }
 
-template <int MODE>
-__device__ __forceinline__ void apply_update(const PieArgs& a, long long oidx, float2 w, float2 dpsi, int pidx) {
-  if (MODE == MODE_COLOURED) {
-    float2 o = a.obj[oidx];
-    const float2 u = cmulc(dpsi, w);  // conj(w) dpsi
-    o.x = fmaf(-a.coef, u.x, o.x);
-    o.y = fmaf(-a.coef, u.y, o.y);
-    a.obj[oidx] = o;
-  } else if (MODE == MODE_BATCHED) {
-    atomicAdd(a.acc + oidx, cscale(cmulc(dpsi, w), a.coef));
+// The pointers of one work item: a position of the single instance, or an
+// (instance, position) pair of a multi-instance sweep.
+struct PieItem {
+  float2* obj;
+  const float2* objr;
+  long long obj_w;
+  const float2* probe;
+  const float* dat;      // this position's amplitudes
+  float coef;
+  float2* acc;
+  double* red;
+  long long obase;       // offset of the patch's top-left pixel
+};
+
+template <int DAT>
+__device__ __forceinline__ PieItem resolve(const PieArgs& a, int it) {
+  PieItem r;
+  if (a.inst) {
+    const int2 w = a.work[it];
+    const PieInstance& in = a.inst[w.x];
+    const int2 rc = in.pos[w.y];
+    r.obj = in.obj;
+    r.objr = in.obj;
+    r.obj_w = in.obj_w;
+    r.probe = in.probe;
+    r.dat = in.dat + (long long)w.y * DAT;
+    r.coef = in.coef;
+    r.acc = in.acc;
+    r.red = in.red;
+    r.obase = (long long)rc.x * in.obj_w + rc.y;
   } else {
-    atomicAdd(a.acc + oidx, cmulc(dpsi, w));
-    if (a.gprobe) atomicAdd(a.gprobe + pidx, cmulc(dpsi, a.objr[oidx]));
+    const int j = a.list ? a.list[it] : it;
+    const int2 rc = a.pos[j];
+    r.obj = a.obj;
+    r.objr = a.objr;
+    r.obj_w = a.obj_w;
+    r.probe = a.probe;
+    r.dat = a.dat + (long long)j * DAT;
+    r.coef = a.coef;
+    r.acc = a.acc;
+    r.red = a.red;
+    r.obase = (long long)rc.x * a.obj_w + rc.y;
+  }
+  return r;
+}
+
+template <int MODE>
+__device__ __forceinline__ void apply_update(const PieArgs& a, const PieItem& p, long long oidx, float2 w,
+                                             float2 dpsi, int pidx) {
+  if (MODE == MODE_COLOURED) {
+    float2 o = p.obj[oidx];
+    const float2 u = cmulc(dpsi, w);  // conj(w) dpsi
+    o.x = fmaf(-p.coef, u.x, o.x);
+    o.y = fmaf(-p.coef, u.y, o.y);
+    p.obj[oidx] = o;
+  } else if (MODE == MODE_BATCHED) {
+    atomicAdd(p.acc + oidx, cscale(cmulc(dpsi, w), p.coef));
+  } else {
+    atomicAdd(p.acc + oidx, cmulc(dpsi, w));
+    if (a.gprobe) atomicAdd(a.gprobe + pidx, cmulc(dpsi, p.objr[oidx]));
   }
 }
 
@@ -160,9 +223,8 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
   LaneNet<P, false> net;
   net.init(k, stw);
   for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
-    const int j = a.list ? a.list[it] : it;
-    const int2 rc = a.pos[j];
-    const long long obase = (long long)rc.x * a.obj_w + rc.y;
+    const PieItem p = resolve<M * M>(a, it);
+    const long long obase = p.obase;
     // 1. rows (axis 2) of the exit wave -> column owners
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int u = r0 + u0 + g;
@@ -170,7 +232,7 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
         const int v = Q * k + l;
-        xv[l] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
+        xv[l] = cmul(__ldg(p.probe + u * N + v), p.objr[obase + (long long)u * p.obj_w + v]);
       }
       T::forward(xv, k, c.bh[1], sW2, net, [&](int t, float2 val) {
         float2* dst = CL::map(sY, (unsigned)(t / CM));
@@ -188,13 +250,13 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
     }
     __syncthreads();
     // 3b. modulus projection on the M x CM coefficients
-    const float* dj = a.dat + (long long)j * (M * M) + rank * CM;
+    const float* dj = p.dat + rank * CM;
     double part = 0.0;
     for (int i = threadIdx.x; i < M * CM; i += NT) {
       float2* z = sZ + (i / CM) * S::ZS + (i % CM);
       *z = residual<MODE>(*z, __ldg(dj + (i / CM) * M + (i % CM)), part);
     }
-    block_accumulate<NT>(part, sred, a.red);
+    block_accumulate<NT>(part, sred, p.red);
     __syncthreads();
     // 3c. adjoint columns -> row owners
     for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
@@ -216,7 +278,7 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
         const int v = Q * k + l;
-        apply_update<MODE>(a, obase + (long long)u * a.obj_w + v, __ldg(a.probe + u * N + v), xv[l], u * N + v);
+        apply_update<MODE>(a, p, obase + (long long)u * p.obj_w + v, __ldg(p.probe + u * N + v), xv[l], u * N + v);
       }
     }
     if constexpr (C == 1) __syncthreads();
@@ -258,9 +320,8 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
   typename F::Net net;
   F::init_net(net, l, tw);
   for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
-    const int j = a.list ? a.list[it] : it;
-    const int2 rc = a.pos[j];
-    const long long obase = (long long)rc.x * a.obj_w + rc.y;
+    const PieItem p = resolve<N * N>(a, it);
+    const long long obase = p.obase;
     // 1. FFT of this CTA's rows of the exit wave -> column-slot owners
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int u = r0 + u0 + g;
@@ -268,7 +329,7 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int v = l + L * e;
-        x[e] = cmul(__ldg(a.probe + u * N + v), a.objr[obase + (long long)u * a.obj_w + v]);
+        x[e] = cmul(__ldg(p.probe + u * N + v), p.objr[obase + (long long)u * p.obj_w + v]);
       }
       F::fwd(x, l, tw, net);
 #pragma unroll
@@ -290,14 +351,14 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
     }
     __syncthreads();
     // 3b. modulus projection
-    const float* dj = a.dat + (long long)j * (N * N);
+    const float* dj = p.dat;
     double part = 0.0;
     for (int i = threadIdx.x; i < N * CN; i += NT) {
       const int sa = i / CN, sb = i % CN;
       float2* z = sC + sa * S::SCS + sb;
       *z = residual<MODE>(*z, __ldg(dj + F::freq_of_slot(sa) * N + F::freq_of_slot(c0 + sb)), part);
     }
-    block_accumulate<NT>(part, sred, a.red);
+    block_accumulate<NT>(part, sred, p.red);
     __syncthreads();
     // 3c. adjoint FFT of the local columns -> row owners (natural row order)
     for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
@@ -323,7 +384,7 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int v = l + L * e;
-        apply_update<MODE>(a, obase + (long long)u * a.obj_w + v, __ldg(a.probe + u * N + v), x[e], u * N + v);
+        apply_update<MODE>(a, p, obase + (long long)u * p.obj_w + v, __ldg(p.probe + u * N + v), x[e], u * N + v);
       }
     }
     if constexpr (C == 1) __syncthreads();

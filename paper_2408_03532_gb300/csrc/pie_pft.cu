@@ -48,6 +48,8 @@ std::vector<Entry> build_table() {
   add_shape<32, 4, 2>(v);   // n = 128, M = 64
   add_shape<16, 16, 2>(v);  // n = 256, M = 32
   add_shape<32, 8, 2>(v);   // n = 256, M = 64
+  add_shape<32, 2, 2>(v);   // n = 64,  M = 64
+  add_shape<8, 32, 2>(v);   // n = 256, M = 16
   return v;
 }
 

@@ -212,6 +212,8 @@ const pfth::FrameKernels g_frame_kernels[] = {
     make_frame_kernels<32, 4, 2>(),  // n = 128, M = 64
     make_frame_kernels<16, 16, 2>(), // n = 256, M = 32
     make_frame_kernels<32, 8, 2>(),  // n = 256, M = 64
+    make_frame_kernels<32, 2, 2>(),  // n = 64,  M = 64
+    make_frame_kernels<8, 32, 2>(),  // n = 256, M = 16
 };
 
 }  // namespace

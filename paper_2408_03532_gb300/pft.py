@@ -106,6 +106,10 @@ def load() -> ctypes.CDLL:
         "pie_nrmse": (ctypes.c_int, [_P, _P, _P, _P, _P]),
         "pie_amp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
+        "pie_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+        "pie_batch_destroy": (ctypes.c_int, [_P]),
+        "pie_batch_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
+        "pie_batch_classes": (ctypes.c_int, [_P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -343,6 +347,71 @@ class PieContext:
     def close(self):
         if getattr(self, "_h", None):
             load().pie_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PieBatch:
+    """Independent PIE problems of different sizes swept together (one graph per sweep).
+
+    Each instance is a dict with keys obj_shape, probe (CUDA complex64 [n, n]),
+    positions (int32 [N, 2]), intensities (CUDA float32 [N, n, n]), M and
+    optionally p and eps.
+    """
+
+    def __init__(self, instances: list[dict], mode: int = MODE_COLOURED, delta_rel: float = 1e-3, stream=None):
+        import torch
+        cnt = len(instances)
+        probs = (PieProblem * cnt)()
+        self._keep = []
+        probes = (ctypes.c_void_p * cnt)()
+        poss = (ctypes.c_void_p * cnt)()
+        ints = (ctypes.c_void_p * cnt)()
+        self.shapes = []
+        for i, inst in enumerate(instances):
+            n = inst["probe"].shape[-1]
+            _need(inst["probe"], torch.complex64, (n, n), "probe")
+            _need(inst["intensities"], torch.float32, (n, n), "intensities")
+            pos = np.ascontiguousarray(np.asarray(inst["positions"], dtype=np.int32).reshape(-1, 2))
+            self._keep.append(pos)
+            h, w = inst["obj_shape"]
+            probs[i] = PieProblem(int(h), int(w), n, len(pos), int(inst["M"]), int(inst.get("p", 0)),
+                                  float(inst.get("eps", 1e-7)), mode, PATH_AUTO, delta_rel, 0)
+            probes[i] = _ptr(inst["probe"])
+            poss[i] = pos.ctypes.data
+            ints[i] = _ptr(inst["intensities"])
+            self.shapes.append((int(h), int(w)))
+        hnd = ctypes.c_void_p()
+        _check(load().pie_batch_create(ctypes.byref(hnd), cnt, probs, probes, poss, ints, _stream(stream)))
+        self._h = hnd
+        self.count = cnt
+
+    def classes(self) -> tuple[int, int]:
+        nc, nl = ctypes.c_int(), ctypes.c_int()
+        _check(load().pie_batch_classes(self._h, ctypes.byref(nc), ctypes.byref(nl)))
+        return nc.value, nl.value
+
+    def iteration(self, objects, transform: int = TRANSFORM_PFT, beta: float = 1.0, stats: bool = True,
+                  stream=None):
+        import torch
+        if len(objects) != self.count:
+            raise ValueError("one object per instance")
+        ptrs = (ctypes.c_void_p * self.count)()
+        for i, o in enumerate(objects):
+            _need(o, torch.complex64, self.shapes[i], f"object {i}")
+            ptrs[i] = _ptr(o)
+        phi = (ctypes.c_double * self.count)() if stats else None
+        _check(load().pie_batch_iteration(self._h, ptrs, transform, beta, phi, _stream(stream)))
+        return list(phi) if stats else None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pie_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

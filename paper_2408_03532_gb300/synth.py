@@ -181,3 +181,48 @@ def gradient_problem() -> dict:
     inten = simulate_intensities(obj, probe, pos, None)
     return dict(obj=obj, probe=probe, pos=pos, intensities=inten, M=32,
                 init=random_init(512))
+
+
+def uneven_batch_recipe(count: int = 64, seed: int = 6, max_side: int = 2048,
+                        sides=(256, 512, 1024, 2048), probes=(64, 128, 256), Ms=(16, 32, 64),
+                        npos=(50, 2000)) -> list[dict]:
+    """Sizes of `count` independent reconstructions: object side uniform in
+    `sides` (<= max_side), probe side uniform in `probes` (< object side), M
+    uniform in `Ms` with M <= probe side, and a uniform number of Fermat-spiral
+    positions in [npos[0], npos[1]]. Each entry also carries its own seeds."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        side = int(rng.choice([s for s in sides if s <= max_side]))
+        n = int(rng.choice([p for p in probes if p < side]))
+        M = int(rng.choice([m for m in Ms if m <= n]))
+        N = int(rng.integers(npos[0], npos[1] + 1))
+        out.append(dict(side=side, n=n, M=M, npos=N, seed=100 + 7 * i))
+    return out
+
+
+def make_instance(spec: dict) -> dict:
+    """Object, probe and scan of one recipe entry (intensities are left to the
+    caller, who may compute them on whichever device suits the size)."""
+    s = spec["seed"]
+    return dict(obj=make_object(spec["side"], seed=s), probe=make_probe(spec["n"], seed=s + 1),
+                pos=fermat_scan(spec["side"], spec["n"], spec["npos"], seed=s + 2),
+                init=random_init(spec["side"], seed=s + 3), M=spec["M"])
+
+
+def simulate_intensities_torch(obj, probe, positions, chunk: int = 256):
+    """|FFT2(probe * patch_j)|^2 (FFT order, float32) computed with torch on the
+    tensors' device; for inputs too large for the numpy route (test input
+    synthesis only)."""
+    import torch
+    n = probe.shape[-1]
+    idx = torch.as_tensor(np.asarray(positions, dtype=np.int64), device=obj.device)
+    ar = torch.arange(n, device=obj.device)
+    out = torch.empty(len(idx), n, n, dtype=torch.float32, device=obj.device)
+    for s in range(0, len(idx), chunk):
+        part = idx[s:s + chunk]
+        rows = part[:, 0, None] + ar[None, :]
+        cols = part[:, 1, None] + ar[None, :]
+        patches = obj[rows[:, :, None], cols[:, None, :]]
+        out[s:s + chunk] = (torch.abs(torch.fft.fft2(probe[None] * patches)) ** 2).float()
+    return out

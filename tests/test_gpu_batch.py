@@ -1,0 +1,105 @@
+"""Independent reconstructions of different sizes swept together (one CUDA
+graph per sweep, one launch per shape class and colour)."""
+import numpy as np
+import pytest
+
+from oracle import coeffs, pie as opie
+from paper_2408_03532_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    from paper_2408_03532_gb300 import build as libbuild
+    from paper_2408_03532_gb300 import pft
+    libbuild.build()
+    pft.load()
+    return torch, pft
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def small_instances():
+    """Six instances over four shape classes, noise-free data."""
+    specs = [dict(side=96, n=32, M=16, npos=40, seed=11), dict(side=160, n=64, M=32, npos=30, seed=12),
+             dict(side=128, n=64, M=16, npos=25, seed=13), dict(side=256, n=128, M=32, npos=20, seed=14),
+             dict(side=100, n=32, M=16, npos=50, seed=15), dict(side=192, n=64, M=32, npos=45, seed=16)]
+    out = []
+    for sp in specs:
+        inst = synth.make_instance(sp)
+        inst["intensities"] = synth.simulate_intensities(inst["obj"], inst["probe"], inst["pos"])
+        out.append(inst)
+    return out
+
+
+def to_gpu(insts, torch):
+    return [dict(obj_shape=i["obj"].shape, probe=torch.from_numpy(i["probe"].astype(np.complex64)).cuda(),
+                 positions=i["pos"], intensities=torch.from_numpy(i["intensities"].astype(np.float32)).cuda(),
+                 M=i["M"]) for i in insts]
+
+
+def oracle_sweep(inst, transform, mode, beta):
+    n, M = inst["probe"].shape[0], inst["M"]
+    start = inst["init"].astype(np.complex64).astype(np.complex128)
+    if transform == "pft":
+        P1, P2 = coeffs.plan_2d(n, n, M, M, M // 2, M // 2)
+        T, d = opie.pft_transform(P1, P2), opie.amplitudes(inst["intensities"], M)
+    else:
+        T, d = opie.full_transform(n, n), opie.amplitudes(inst["intensities"])
+    if mode == "coloured":
+        order = opie.colour_major_order(opie.greedy_colouring(inst["pos"], n, n))
+        return opie.pie_sweep(start, inst["probe"], inst["pos"], d, T, beta, order)
+    return opie.batched_sweep(start, inst["probe"], inst["pos"], d, T, beta, delta_rel=1e-3)
+
+
+@pytest.mark.parametrize("mode", ["coloured", "batched"])
+@pytest.mark.parametrize("transform", ["pft", "full"])
+def test_small_batch_matches_oracle_per_instance(env, mode, transform):
+    torch, pft = env
+    insts = small_instances()
+    B = pft.PieBatch(to_gpu(insts, torch), mode=pft.MODE_COLOURED if mode == "coloured" else pft.MODE_BATCHED)
+    assert B.classes()[0] == 4
+    objs = [torch.from_numpy(i["init"].astype(np.complex64)).cuda() for i in insts]
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    phi = B.iteration(objs, tr, 0.9)
+    for i, inst in enumerate(insts):
+        zo, po = oracle_sweep(inst, transform, mode, 0.9)
+        assert rel(objs[i].cpu().numpy(), zo) < TOL, i
+        assert phi[i] == pytest.approx(po, rel=TOL)
+
+
+def test_batch_equals_separate_contexts_at_full_recipe(env):
+    """The 64-instance recipe (objects 256^2-2048^2, probes 64^2-256^2, 50-2000
+    Fermat positions, M in {16, 32, 64}): one batched PFT sweep gives, instance
+    by instance, exactly the object of a sweep with a context of its own (the
+    same kernel on the same data; only the launch grouping differs)."""
+    torch, pft = env
+    specs = synth.uneven_batch_recipe(64)
+    insts = []
+    for sp in specs:
+        inst = synth.make_instance(sp)
+        obj = torch.from_numpy(inst["obj"].astype(np.complex64)).cuda()
+        pr = torch.from_numpy(inst["probe"].astype(np.complex64)).cuda()
+        inten = synth.simulate_intensities_torch(obj, pr, inst["pos"])
+        insts.append(dict(obj_shape=inst["obj"].shape, probe=pr, positions=inst["pos"],
+                          intensities=inten, M=sp["M"], init=inst["init"]))
+    B = pft.PieBatch(insts)
+    nclass, nlaunch = B.classes()
+    assert nclass >= 5
+    objs = [torch.from_numpy(i["init"].astype(np.complex64)).cuda() for i in insts]
+    B.iteration(objs, pft.TRANSFORM_PFT, 1.0, stats=False)
+    torch.cuda.synchronize()
+    for i in (0, 17, 41, 63):
+        ctx = pft.PieContext(insts[i]["obj_shape"], insts[i]["probe"], insts[i]["positions"],
+                             insts[i]["intensities"], M=insts[i]["M"], autotune=False)
+        z = torch.from_numpy(insts[i]["init"].astype(np.complex64)).cuda()
+        ctx.iteration(z, pft.TRANSFORM_PFT, 1.0, stats=False)
+        torch.cuda.synchronize()
+        assert torch.equal(z, objs[i]), i

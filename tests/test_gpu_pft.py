@@ -9,7 +9,8 @@ from paper_2408_03532_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-SHAPES = [(32, 16), (64, 16), (64, 32), (128, 16), (128, 32), (128, 64), (256, 32), (256, 64)]
+SHAPES = [(32, 16), (64, 16), (64, 32), (64, 64), (128, 16), (128, 32), (128, 64), (256, 16), (256, 32),
+          (256, 64)]
 
 
 @pytest.fixture(scope="module")
