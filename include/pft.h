@@ -222,6 +222,8 @@ typedef struct pie_schedule {
   double beta_pft, beta_full;
   double tol_pft, tol_full;
   int max_pft, max_full;
+  double tv_pft, tv_full;  /* TV weights (0 = none): one pie_tv_step after each sweep */
+  double tv_eps;           /* TV smoothing (0 = 1e-3)                                 */
 } pie_schedule;
 
 typedef struct pie_trace {
@@ -232,6 +234,21 @@ typedef struct pie_trace {
 
 int warm_start_then_refine(pie_ctx* ctx, void* object, const pie_schedule* schedule,
                            const void* truth, pie_trace* trace, int* ntrace, void* stream);
+
+/* Total-variation regularisation (Section 4 regularises both phases with TV;
+ * the term is not spelled out there). One gradient step on the smoothed
+ * isotropic TV, in place on `object`:
+ *   z <- z - lambda (D_x^H(D_x z / s) + D_y^H(D_y z / s)),
+ *   s = sqrt(|D_x z|^2 + |D_y z|^2 + eps^2),
+ * forward differences, zero flux across the last row and column. */
+int pie_tv_step(pie_ctx* ctx, void* object, double lambda, double eps, void* stream);
+
+/* Visiting order of the scan positions (the blind experiments of Section 4.2
+ * draw a random order without replacement). order: host int32 [N], a
+ * permutation of 0..N-1, or NULL for index order. The positions are
+ * re-coloured greedily in that order and every sweep then runs colour-major
+ * with that order inside each colour. Synchronises the device. */
+int pie_ctx_set_order(pie_ctx* ctx, const int32_t* order);
 
 /* Phase-aligned error min_phi ||e^{i phi} z - truth|| / ||truth|| over the
  * context's illuminated mask (FP64 on the GPU); synchronises `stream`. */

@@ -140,14 +140,16 @@ def overlaps(a, b, n1: int, n2: int) -> bool:
     return abs(int(a[0]) - int(b[0])) < n1 and abs(int(a[1]) - int(b[1])) < n2
 
 
-def greedy_colouring(positions: np.ndarray, n1: int, n2: int) -> np.ndarray:
-    """Greedy colouring in index order: each position takes the smallest colour
-    not used by an earlier position whose patch overlaps its own."""
+def greedy_colouring(positions: np.ndarray, n1: int, n2: int, order=None) -> np.ndarray:
+    """Greedy colouring: positions are visited in ``order`` (index order by
+    default) and each takes the smallest colour not used by an earlier-visited
+    position whose patch overlaps its own."""
     N = len(positions)
+    order = np.arange(N) if order is None else np.asarray(order)
     col = np.full(N, -1, dtype=np.int64)
-    for j in range(N):
+    for a, j in enumerate(order):
         used = set()
-        for i in range(j):
+        for i in order[:a]:
             if overlaps(positions[i], positions[j], n1, n2):
                 used.add(int(col[i]))
         k = 0
@@ -157,9 +159,13 @@ def greedy_colouring(positions: np.ndarray, n1: int, n2: int) -> np.ndarray:
     return col
 
 
-def colour_major_order(colours: np.ndarray) -> np.ndarray:
-    """Positions sorted by colour, index order within a colour."""
-    return np.lexsort((np.arange(len(colours)), colours))
+def colour_major_order(colours: np.ndarray, order=None) -> np.ndarray:
+    """Positions sorted by colour, in visiting order (index order by default)
+    within a colour."""
+    N = len(colours)
+    rank = np.empty(N, dtype=np.int64)
+    rank[np.arange(N) if order is None else np.asarray(order)] = np.arange(N)
+    return np.lexsort((rank, colours))
 
 
 # ---------------------------------------------------------------------------
@@ -198,9 +204,12 @@ def nrmse(z: np.ndarray, truth: np.ndarray, mask: np.ndarray | None = None) -> f
 def hybrid_pie(init: np.ndarray, probe: np.ndarray, positions: np.ndarray,
                intensities: np.ndarray, T_pft: dict, M: int, beta_pft: float, beta_full: float,
                tol_pft: float, max_pft: int, tol_full: float, max_full: int,
-               order=None, truth: np.ndarray | None = None) -> tuple[np.ndarray, list]:
+               order=None, truth: np.ndarray | None = None, tv_pft: float = 0.0, tv_full: float = 0.0,
+               tv_eps: float = 1e-3) -> tuple[np.ndarray, list]:
     """Algorithm 3: crop the data, PFT-PIE until tol_pft or max_pft sweeps,
-    then full-FFT PIE from that point until tol_full or max_full sweeps.
+    then full-FFT PIE from that point until tol_full or max_full sweeps. With
+    a TV weight, each sweep of that phase is followed by one TV gradient step
+    (Section 4 regularises both phases, the PFT phase more strongly).
 
     Returns (z, trace) with one dict per sweep: phase, Phi, relative change and
     (with a truth) the phase-aligned error on the illuminated mask.
@@ -212,10 +221,13 @@ def hybrid_pie(init: np.ndarray, probe: np.ndarray, positions: np.ndarray,
     mask = illuminated_mask(probe, positions, init.shape) if truth is not None else None
     z = np.array(init, dtype=np.complex128, copy=True)
     trace = []
-    for phase, T, data, beta, tol, mx in (("pft", T_pft, d_crop, beta_pft, tol_pft, max_pft),
-                                           ("full", T_full, d_full, beta_full, tol_full, max_full)):
+    from . import tv as _tv
+    for phase, T, data, beta, tol, mx, lam in (("pft", T_pft, d_crop, beta_pft, tol_pft, max_pft, tv_pft),
+                                                ("full", T_full, d_full, beta_full, tol_full, max_full, tv_full)):
         for _ in range(mx):                                  # steps 2 and 3
             z_new, phi = pie_sweep(z, probe, positions, data, T, beta, order)
+            if lam > 0.0:
+                z_new = _tv.tv_step(z_new, lam, tv_eps)
             ch = relative_change(z_new, z)
             z = z_new
             rec = dict(phase=phase, phi=phi, change=ch)

@@ -118,6 +118,44 @@ __global__ void k_apply_batched(float2* __restrict__ z, const float2* __restrict
   }
 }
 
+// One gradient step of the smoothed isotropic total variation,
+//   out = z - lambda (D_x^H(D_x z / s) + D_y^H(D_y z / s)),
+//   s = sqrt(|D_x z|^2 + |D_y z|^2 + eps^2),
+// forward differences with zero flux across the last row and column.
+__device__ __forceinline__ void tv_terms(const float2* __restrict__ z, int H, int W, int i, int j, float eps2,
+                                         float2& u, float2& v) {
+  const float2 c = z[(long long)i * W + j];
+  const float2 a = j + 1 < W ? csub(z[(long long)i * W + j + 1], c) : make_float2(0.f, 0.f);
+  const float2 b = i + 1 < H ? csub(z[(long long)(i + 1) * W + j], c) : make_float2(0.f, 0.f);
+  const float inv = rsqrtf(cabs2(a) + cabs2(b) + eps2);
+  u = cscale(a, inv);
+  v = cscale(b, inv);
+}
+
+__global__ void k_tv_step(const float2* __restrict__ z, float2* __restrict__ out, int H, int W, float lam,
+                          float eps) {
+  const long long n = (long long)H * W;
+  const float eps2 = eps * eps;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p / W), j = (int)(p % W);
+    float2 u, v, ul, vu, tmp;
+    tv_terms(z, H, W, i, j, eps2, u, v);
+    float2 g = make_float2(0.f, 0.f);
+    if (j + 1 < W) g = csub(g, u);          // -u[i, j]
+    if (i + 1 < H) g = csub(g, v);          // -v[i, j]
+    if (j > 0) {                            // +u[i, j-1]
+      tv_terms(z, H, W, i, j - 1, eps2, ul, tmp);
+      g = cadd(g, ul);
+    }
+    if (i > 0) {                            // +v[i-1, j]
+      tv_terms(z, H, W, i - 1, j, eps2, tmp, vu);
+      g = cadd(g, vu);
+    }
+    const float2 c = z[p];
+    out[p] = make_float2(fmaf(-lam, g.x, c.x), fmaf(-lam, g.y, c.y));
+  }
+}
+
 int grid_for(long long work) {
   long long g = (work + kThreads - 1) / kThreads;
   long long cap = 8LL * pfth::sm_count();
@@ -143,13 +181,15 @@ struct pie_ctx {
   std::vector<int2> h_pos;
   float* d_amp = nullptr;      // [N][n][n]
   float* d_ampc = nullptr;     // [N][M][M]
-  std::vector<int> colour, col_off;
+  std::vector<int> colour, col_off, visit;
   int ncol = 0;
   int* d_sched = nullptr;
   float* d_inv_illum = nullptr;
   unsigned char* d_mask = nullptr;
   float2* d_prev = nullptr;
   float2* d_acc = nullptr;
+  float2* d_tv = nullptr;      // TV step scratch (allocated on first use)
+  float2* d_start = nullptr;   // object at the start of a regularised sweep
   double* d_red = nullptr;     // [8]
   double* h_red = nullptr;     // pinned [8]
   // captured sweeps, replayed on the caller's stream
@@ -194,9 +234,10 @@ int prepare_kernel(const PieKernel& k, long long* cap) {
   return PFT_OK;
 }
 
-// Greedy colouring in index order (smallest colour unused by an earlier
-// overlapping patch); colour-major schedule, index order within a colour.
-void colour_positions(pie_ctx* c) {
+// Greedy colouring in visiting order (smallest colour unused by an earlier
+// visited overlapping patch); colour-major schedule, visiting order within a
+// colour. `order` is a permutation of 0..N-1 (empty: index order).
+void colour_positions(pie_ctx* c, const std::vector<int>& order = {}) {
   const int N = c->npos, n = c->n;
   c->colour.assign(N, -1);
   // bucket positions by n x n cells so only neighbouring cells are scanned
@@ -204,7 +245,10 @@ void colour_positions(pie_ctx* c) {
   std::vector<std::vector<int>> cells((size_t)cw * ch);
   std::vector<char> used;
   int ncol = 0;
-  for (int j = 0; j < N; ++j) {
+  c->visit.resize(N);
+  for (int a = 0; a < N; ++a) c->visit[a] = order.empty() ? a : order[a];
+  for (int a = 0; a < N; ++a) {
+    const int j = c->visit[a];
     const int2 p = c->h_pos[j];
     const int cx = p.y / n, cy = p.x / n;
     used.assign(ncol + 1, 0);
@@ -232,6 +276,16 @@ void colour_positions(pie_ctx* c) {
 // Launches the fused kernel for `a.count` positions. Coloured sweeps pick the
 // largest cluster size whose CTAs for all positions of the colour fit on the
 // GPU at once; the other modes run one CTA per position.
+// Colour-major schedule (visiting order inside a colour) to the device.
+int upload_schedule(pie_ctx* c, cudaStream_t st) {
+  std::vector<int> sched(c->npos);
+  std::vector<int> fill(c->col_off.begin(), c->col_off.end() - 1);
+  for (int j : c->visit) sched[fill[c->colour[j]]++] = j;
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(int) * c->npos, cudaMemcpyHostToDevice, st));
+  PFT_CUDA_TRY(cudaStreamSynchronize(st));
+  return PFT_OK;
+}
+
 int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) {
   if (a.count <= 0) return PFT_OK;
   const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
@@ -343,6 +397,8 @@ int pie_ctx_destroy(pie_ctx* c) {
   cudaFree(c->d_mask);
   cudaFree(c->d_prev);
   cudaFree(c->d_acc);
+  cudaFree(c->d_tv);
+  cudaFree(c->d_start);
   cudaFree(c->d_red);
   if (c->h_red) cudaFreeHost(c->h_red);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -446,13 +502,8 @@ int pie_ctx_create(pie_ctx** out, const pie_problem* pb, const void* probe, cons
   PIE_CUDA(cudaGetLastError());
   // colouring
   colour_positions(c);
-  std::vector<int> sched(N);
-  {
-    std::vector<int> fill(c->col_off.begin(), c->col_off.end() - 1);
-    for (int j = 0; j < N; ++j) sched[fill[c->colour[j]]++] = j;
-  }
   PIE_CUDA(cudaMalloc(&c->d_sched, sizeof(int) * N));
-  PIE_CUDA(cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  PIE_TRY(upload_schedule(c, st));
   // illumination, inverse illumination, mask
   const long long HW = (long long)H * W;
   PIE_CUDA(cudaMalloc(&c->d_inv_illum, sizeof(float) * HW));
@@ -605,6 +656,39 @@ int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stat
   return PFT_OK;
 }
 
+int pie_tv_step(pie_ctx* c, void* object, double lambda, double eps, void* stream) {
+  if (!c || !object) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (!(lambda >= 0.0) || !(eps >= 0.0)) return pfth::set_error(PFT_ERR_INVALID_ARG, "need lambda, eps >= 0");
+  if (lambda == 0.0) return PFT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long HW = (long long)c->H * c->W;
+  if (!c->d_tv) PFT_CUDA_TRY(cudaMalloc(&c->d_tv, sizeof(float2) * HW));
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_tv, object, sizeof(float2) * HW, cudaMemcpyDeviceToDevice, st));
+  k_tv_step<<<grid_for(HW), kThreads, 0, st>>>(c->d_tv, (float2*)object, c->H, c->W, (float)lambda, (float)eps);
+  PFT_CUDA_TRY(cudaGetLastError());
+  return PFT_OK;
+}
+
+int pie_ctx_set_order(pie_ctx* c, const int32_t* order) {
+  if (!c) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  std::vector<int> ord;
+  if (order) {
+    ord.assign(order, order + c->npos);
+    std::vector<char> seen(c->npos, 0);
+    for (int j : ord) {
+      if (j < 0 || j >= c->npos || seen[j]) return pfth::set_error(PFT_ERR_INVALID_ARG, "order is not a permutation");
+      seen[j] = 1;
+    }
+  }
+  PFT_CUDA_TRY(cudaDeviceSynchronize());  // no sweep of the old schedule may still be running
+  colour_positions(c, ord);
+  int rc = upload_schedule(c, nullptr);
+  if (rc != PFT_OK) return rc;
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  return PFT_OK;
+}
+
 int pie_nrmse(pie_ctx* c, const void* object, const void* truth, double* out, void* stream) {
   if (!c || !object || !truth || !out) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
@@ -629,14 +713,31 @@ int warm_start_then_refine(pie_ctx* c, void* object, const pie_schedule* s, cons
   if (ntrace) *ntrace = 0;
   const auto t0 = std::chrono::steady_clock::now();
   int cnt = 0;
-  const struct { int tr; double beta, tol; int mx; } phases[2] = {
-      {PIE_TRANSFORM_PFT, s->beta_pft, s->tol_pft, s->max_pft},
-      {PIE_TRANSFORM_FULL, s->beta_full, s->tol_full, s->max_full}};
+  const struct { int tr; double beta, tol; int mx; double tv; } phases[2] = {
+      {PIE_TRANSFORM_PFT, s->beta_pft, s->tol_pft, s->max_pft, s->tv_pft},
+      {PIE_TRANSFORM_FULL, s->beta_full, s->tol_full, s->max_full, s->tv_full}};
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long HW = (long long)c->H * c->W;
   for (const auto& ph : phases) {
+    if (ph.tv < 0.0) return pfth::set_error(PFT_ERR_INVALID_ARG, "negative TV weight");
+    if (ph.tv > 0.0 && !c->d_start) PFT_CUDA_TRY(cudaMalloc(&c->d_start, sizeof(float2) * HW));
     for (int it = 0; it < ph.mx; ++it) {
       pie_stats stt;
+      if (ph.tv > 0.0)
+        PFT_CUDA_TRY(cudaMemcpyAsync(c->d_start, object, sizeof(float2) * HW, cudaMemcpyDeviceToDevice, st));
       int rc = pie_iteration(c, object, ph.tr, ph.beta, &stt, stream);
       if (rc != PFT_OK) return rc;
+      if (ph.tv > 0.0) {
+        // one TV gradient step after the sweep; the stopping rule sees the regularised object
+        rc = pie_tv_step(c, object, ph.tv, s->tv_eps > 0 ? s->tv_eps : 1e-3, stream);
+        if (rc != PFT_OK) return rc;
+        PFT_CUDA_TRY(cudaMemsetAsync(c->d_red + 1, 0, sizeof(double) * 2, st));
+        k_diff_norms<<<grid_for(HW), kThreads, 0, st>>>((const float2*)object, c->d_start, HW, c->d_red + 1);
+        PFT_CUDA_TRY(cudaGetLastError());
+        PFT_CUDA_TRY(cudaMemcpyAsync(c->h_red + 1, c->d_red + 1, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+        PFT_CUDA_TRY(cudaStreamSynchronize(st));
+        stt.rel_change = c->h_red[2] > 0 ? std::sqrt(c->h_red[1] / c->h_red[2]) : 0.0;
+      }
       double e = NAN;
       if (truth) {
         rc = pie_nrmse(c, object, truth, &e, stream);

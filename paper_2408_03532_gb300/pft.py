@@ -56,7 +56,8 @@ class PieStats(ctypes.Structure):
 
 class PieSchedule(ctypes.Structure):
     _fields_ = [("beta_pft", ctypes.c_double), ("beta_full", ctypes.c_double), ("tol_pft", ctypes.c_double),
-                ("tol_full", ctypes.c_double), ("max_pft", ctypes.c_int), ("max_full", ctypes.c_int)]
+                ("tol_full", ctypes.c_double), ("max_pft", ctypes.c_int), ("max_full", ctypes.c_int),
+                ("tv_pft", ctypes.c_double), ("tv_full", ctypes.c_double), ("tv_eps", ctypes.c_double)]
 
 
 class PieTrace(ctypes.Structure):
@@ -104,6 +105,8 @@ def load() -> ctypes.CDLL:
         "pie_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
         "warm_start_then_refine": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+        "pie_tv_step": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, _P]),
+        "pie_ctx_set_order": (ctypes.c_int, [_P, _P]),
         "pie_amp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
         "pie_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
@@ -269,6 +272,9 @@ class Schedule:
     tol_full: float = 5e-4
     max_pft: int = 50
     max_full: int = 100
+    tv_pft: float = 0.0
+    tv_full: float = 0.0
+    tv_eps: float = 1e-3
 
 
 class PieContext:
@@ -312,6 +318,21 @@ class PieContext:
                                     ctypes.byref(st) if stats else None, _stream(stream)))
         return {"phi": st.phi, "rel_change": st.rel_change} if stats else None
 
+    def tv_step(self, obj, lam: float, eps: float = 1e-3, stream=None):
+        """One total-variation gradient step on obj, in place."""
+        self._obj(obj)
+        _check(load().pie_tv_step(self._h, _ptr(obj), lam, eps, _stream(stream)))
+
+    def set_order(self, order=None):
+        """Visit the positions in `order` (a permutation; None = index order)."""
+        if order is None:
+            _check(load().pie_ctx_set_order(self._h, None))
+            return
+        o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+        if o.shape != (self.npos,):
+            raise ValueError("order must be a permutation of the positions")
+        _check(load().pie_ctx_set_order(self._h, o.ctypes.data))
+
     def nrmse(self, obj, truth, stream=None) -> float:
         self._obj(obj)
         self._obj(truth, "truth")
@@ -324,7 +345,7 @@ class PieContext:
         if truth is not None:
             self._obj(truth, "truth")
         s = PieSchedule(schedule.beta_pft, schedule.beta_full, schedule.tol_pft, schedule.tol_full,
-                        schedule.max_pft, schedule.max_full)
+                        schedule.max_pft, schedule.max_full, schedule.tv_pft, schedule.tv_full, schedule.tv_eps)
         cap = max(1, schedule.max_pft + schedule.max_full)
         tr = (PieTrace * cap)()
         cnt = ctypes.c_int()

@@ -253,3 +253,58 @@ def test_autograd_function_matches_oracle_and_fd(env):
         fd = ograd.finite_difference(lambda zz: ograd.amplitude_loss(zz, w64, pos[cover], d[cover], T),
                                      z64, (r, c), 1e-6)
         assert abs(gz[r, c] - fd) <= 1e-5 * scale
+
+
+def test_tv_step_matches_oracle(env, small):
+    """One TV gradient step (Section 4's regulariser, smoothed isotropic TV) on a
+    non-square object: the GPU's gradient (z - z_new)/lambda matches the oracle's."""
+    torch, pft = env
+    from oracle import tv as otv
+    rng = np.random.default_rng(8)
+    obj = synth.make_object(96)[:80, :96] * np.exp(0.3j) + 0.05 * (rng.standard_normal((80, 96)))
+    probe = synth.make_probe(32)
+    pos = synth.raster_scan(2, 3, 24, 0)
+    inten = synth.simulate_intensities(obj, probe, pos)
+    ctx = pft.PieContext(obj.shape, c64(probe, torch), pos, torch.from_numpy(inten.astype(np.float32)).cuda(), M=16)
+    z = c64(obj, torch)
+    z0 = z.clone()
+    ctx.tv_step(z, 0.01, 0.05)
+    g_gpu = (z0 - z).cpu().numpy().astype(np.complex128) / 0.01
+    g_ref = otv.tv_grad(obj.astype(np.complex64).astype(np.complex128), 0.05)
+    assert rel(g_gpu, g_ref) < 1e-4
+
+
+def test_random_order_sweep_matches_oracle(env, small):
+    """A seeded random visiting order (the blind experiments' order without
+    replacement) on the noise-free raster problem: the re-colouring and the
+    sweep match the oracle."""
+    torch, pft = env
+    P = small
+    ctx = make_ctx(P, torch, pft)
+    order = np.random.default_rng(17).permutation(len(P["pos"]))
+    ctx.set_order(order)
+    col = opie.greedy_colouring(P["pos"], 32, 32, order)
+    assert np.array_equal(ctx.colours(), col)
+    z = c64(P["init"], torch)
+    ctx.iteration(z, pft.TRANSFORM_PFT, 1.0)
+    T, d = oracle_T(P, "pft")
+    zo, _ = opie.pie_sweep(P["init"], P["probe"], P["pos"], d, T, 1.0, opie.colour_major_order(col, order))
+    assert rel(z.cpu().numpy(), zo) < TOL
+
+
+def test_hybrid_with_tv_matches_oracle(env, small):
+    """Algorithm 3 with a TV step after every sweep (stronger in the PFT phase)."""
+    torch, pft = env
+    P = small
+    ctx = make_ctx(P, torch, pft)
+    z = c64(P["init"], torch)
+    tr = ctx.warm_start_then_refine(z, pft.Schedule(1.0, 1.0, 0.0, 0.0, 5, 5, tv_pft=1e-2, tv_full=1e-4,
+                                                    tv_eps=1e-2), c64(P["obj"], torch))
+    T, _ = oracle_T(P, "pft")
+    order = opie.colour_major_order(opie.greedy_colouring(P["pos"], 32, 32))
+    zo, tro = opie.hybrid_pie(P["init"], P["probe"], P["pos"], P["intensities"], T, P["M"], 1.0, 1.0, 0.0, 5,
+                              0.0, 5, order=order, truth=P["obj"], tv_pft=1e-2, tv_full=1e-4, tv_eps=1e-2)
+    for g, o in zip(tr, tro):
+        assert abs(g["nrmse"] - o["nrmse"]) < 1e-4
+        assert g["rel_change"] == pytest.approx(o["change"], rel=1e-3)
+    assert rel(z.cpu().numpy(), zo) < 1e-4

@@ -137,3 +137,20 @@ def test_hybrid_runs_both_phases_and_stops_on_tolerance():
     assert phases[:4] == ["pft"] * 4 and phases[4] == "full"
     assert tr[-1]["change"] < 0.05 or len(tr) == 34
     assert all("nrmse" in t for t in tr)
+
+
+def test_colouring_in_a_given_order():
+    """Visiting order changes the greedy colouring but not its validity; the
+    colour-major order keeps the visiting order inside each colour."""
+    pos = synth.fermat_scan(256, 32, 120)
+    order = np.random.default_rng(3).permutation(120)
+    col = pie.greedy_colouring(pos, 32, 32, order)
+    for a, j in enumerate(order):
+        for i in order[:a]:
+            if pie.overlaps(pos[i], pos[j], 32, 32):
+                assert col[i] != col[j]
+    cm = pie.colour_major_order(col, order)
+    rank = {int(j): a for a, j in enumerate(order)}
+    for x, y in zip(cm, cm[1:]):
+        assert col[x] < col[y] or (col[x] == col[y] and rank[int(x)] < rank[int(y)])
+    assert np.array_equal(pie.greedy_colouring(pos, 32, 32, np.arange(120)), pie.greedy_colouring(pos, 32, 32))
