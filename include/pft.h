@@ -211,6 +211,22 @@ int pie_ctx_colours(const pie_ctx* ctx, int* ncolours, int32_t* colour_of);
 int pie_iteration(pie_ctx* ctx, void* object, int transform, double beta,
                   pie_stats* stats, void* stream);
 
+/* Blind PIE (Eq. pie_update with Eq. epie_probe_update), coloured mode only:
+ * one sweep that also refines the context's probe. Within a colour every
+ * position uses the probe of the colour's start and updates its patch; the
+ * probe step of Eq. epie_probe_update is then evaluated at each updated patch,
+ * g_j = conj(z_j) (w z_j - P_M(z_j)) (a second transform pair per position),
+ * and after the colour w <- w - gamma sum_j g_j / (sum_j |z_j|^2 + delta),
+ * delta = delta_rel max(sum_j |z_j|^2). The object step is
+ * beta conj(w) / max|w|^2 with the probe of that colour. */
+int pie_iteration_blind(pie_ctx* ctx, void* object, int transform, double beta, double gamma,
+                        pie_stats* stats, void* stream);
+
+/* Copy the context's current probe into `probe_out` (device [n][n] complex),
+ * or replace it with `probe` (device, copied; synchronises `stream`). */
+int pie_ctx_probe(const pie_ctx* ctx, void* probe_out, void* stream);
+int pie_ctx_set_probe(pie_ctx* ctx, const void* probe, void* stream);
+
 /* Algorithm 3: PFT sweeps until rel_change < tol_pft or max_pft sweeps, then
  * full-FFT sweeps until rel_change < tol_full or max_full sweeps.
  * truth: optional device [obj_h][obj_w] complex; with it each trace entry also

@@ -131,6 +131,42 @@ def illumination(probe: np.ndarray, positions: np.ndarray, shape) -> np.ndarray:
     return out
 
 
+def epie_colour_sweep(obj: np.ndarray, probe: np.ndarray, positions: np.ndarray, data: np.ndarray,
+                      T: dict, beta: float, gamma: float, colours: np.ndarray, order=None,
+                      delta_rel: float = 1e-3) -> tuple[np.ndarray, np.ndarray, float]:
+    """Blind PIE (Eq. pie_update and Eq. epie_probe_update), colour-synchronous.
+
+    Reading: the probe is shared by every position, so positions that run
+    together cannot each see the probe left by the previous one. Within a colour
+    every position uses the probe w of the colour's start and updates its patch
+    (Eq. pie_update); then the probe step of Eq. epie_probe_update is evaluated at
+    the updated patch z_j^{k+1},
+        g_j = conj(z_j^{k+1}) . (w . z_j^{k+1} - P_M(z_j^{k+1})),
+    and the colour's steps are summed and normalised pixel by pixel:
+        w <- w - gamma * sum_j g_j / (sum_j |z_j^{k+1}|^2 + delta),
+    delta = delta_rel * max of that sum. Returns (z, w, Phi)."""
+    n1, n2 = probe.shape
+    z = np.array(obj, dtype=np.complex128, copy=True)
+    w = np.array(probe, dtype=np.complex128, copy=True)
+    cm = colour_major_order(colours, order)
+    tot = 0.0
+    for c in range(int(colours.max()) + 1):
+        members = [j for j in cm if colours[j] == c]
+        wmax2 = float(np.max(np.abs(w) ** 2))
+        for j in members:
+            tot += pie_update(z, w, positions[j], data[j], T, beta, wmax2)
+        acc = np.zeros_like(w)
+        den = np.zeros(w.shape)
+        for j in members:
+            r, cc = positions[j]
+            zj = z[r:r + n1, cc:cc + n2]
+            R = residual(T["fwd"](w * zj), data[j])
+            acc += np.conj(zj) * T["adj"](R) / (n1 * n2)
+            den += np.abs(zj) ** 2
+        w = w - gamma * acc / (den + delta_rel * den.max())
+    return z, w, tot / len(positions)
+
+
 # ---------------------------------------------------------------------------
 # position colouring (overlap-free classes)
 # ---------------------------------------------------------------------------

@@ -156,6 +156,66 @@ __global__ void k_tv_step(const float2* __restrict__ z, float2* __restrict__ out
   }
 }
 
+// Blind PIE: max |w|^2 of the probe, and empty accumulators (single block).
+__global__ void k_probe_init(const float2* __restrict__ w, int n2, float2* __restrict__ acc,
+                             float* __restrict__ den, float* __restrict__ scale) {
+  __shared__ float red[32];
+  float m = 0.f;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    m = fmaxf(m, cabs2(w[i]));
+    acc[i] = make_float2(0.f, 0.f);
+    den[i] = 0.f;
+  }
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(PFT_FULL_MASK, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmaxf(t, red[i]);
+    *scale = t;
+  }
+}
+
+// Blind PIE, end of a colour: w <- w - gamma acc / (den + delta_rel max den),
+// then the new max |w|^2 and empty accumulators (single block).
+__global__ void k_probe_apply(float2* __restrict__ w, int n2, float2* __restrict__ acc, float* __restrict__ den,
+                              float gamma, float delta_rel, float* __restrict__ scale) {
+  __shared__ float red[32];
+  __shared__ float dmax;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) m = fmaxf(m, den[i]);
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(PFT_FULL_MASK, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmaxf(t, red[i]);
+    dmax = t;
+  }
+  __syncthreads();
+  const float delta = delta_rel * dmax;
+  float pm = 0.f;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    const float s = gamma / (den[i] + delta);
+    float2 v = w[i];
+    v.x = fmaf(-s, acc[i].x, v.x);
+    v.y = fmaf(-s, acc[i].y, v.y);
+    w[i] = v;
+    pm = fmaxf(pm, cabs2(v));
+    acc[i] = make_float2(0.f, 0.f);
+    den[i] = 0.f;
+  }
+  for (int o = 16; o; o >>= 1) pm = fmaxf(pm, __shfl_xor_sync(PFT_FULL_MASK, pm, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = fmaxf(t, red[i]);
+    *scale = t;
+  }
+}
+
 int grid_for(long long work) {
   long long g = (work + kThreads - 1) / kThreads;
   long long cap = 8LL * pfth::sm_count();
@@ -189,6 +249,9 @@ struct pie_ctx {
   float2* d_prev = nullptr;
   float2* d_acc = nullptr;
   float2* d_tv = nullptr;      // TV step scratch (allocated on first use)
+  float2* d_pacc = nullptr;    // blind PIE probe-step accumulators (allocated on first use)
+  float* d_pden = nullptr;
+  float* d_pscale = nullptr;
   float2* d_start = nullptr;   // object at the start of a regularised sweep
   double* d_red = nullptr;     // [8]
   double* h_red = nullptr;     // pinned [8]
@@ -197,6 +260,7 @@ struct pie_ctx {
     const void* obj;
     int transform;
     double beta;
+    double gamma;  // < 0: non-blind
     bool stats;
     cudaGraphExec_t exec;
   };
@@ -330,7 +394,8 @@ int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) 
   return PFT_OK;
 }
 
-int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st);
+int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st,
+                  double gamma = -1.0);
 
 __global__ void k_fill(float2* __restrict__ z, long long n, float2 v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -399,6 +464,9 @@ int pie_ctx_destroy(pie_ctx* c) {
   cudaFree(c->d_acc);
   cudaFree(c->d_tv);
   cudaFree(c->d_start);
+  cudaFree(c->d_pacc);
+  cudaFree(c->d_pden);
+  cudaFree(c->d_pscale);
   cudaFree(c->d_red);
   if (c->h_red) cudaFreeHost(c->h_red);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
@@ -557,12 +625,15 @@ namespace {
 // Enqueues one sweep on `st`: statistics buffers, the kernels of every colour
 // (or the batched kernel and its update), and with `stats` the FP64 norms and
 // their copy to pinned host memory.
-int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st) {
+int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st,
+                  double gamma) {
   const long long HW = (long long)c->H * c->W;
+  const bool blind = gamma >= 0.0;
+  const int n2i = c->n * c->n;
   if (stats) PFT_CUDA_TRY(cudaMemcpyAsync(c->d_prev, obj, sizeof(float2) * HW, cudaMemcpyDeviceToDevice, st));
   PFT_CUDA_TRY(cudaMemsetAsync(c->d_red, 0, sizeof(double) * 8, st));
   const float n2 = (float)c->n * (float)c->n;
-  PieArgs a;
+  PieArgs a = {};
   a.inst = nullptr;
   a.work = nullptr;
   a.obj = obj;
@@ -576,11 +647,25 @@ int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stat
   if (c->pb.mode == PIE_MODE_COLOURED) {
     a.coef = (float)(beta / ((double)c->probe_max2 * n2));
     a.acc = nullptr;
+    if (blind) {
+      // the probe changes after every colour: the object step reads max |w|^2 from the device
+      a.coef = (float)(beta / n2);
+      a.pacc = c->d_pacc;
+      a.pden = c->d_pden;
+      a.pscale = c->d_pscale;
+      k_probe_init<<<1, 1024, 0, st>>>(c->d_probe, n2i, c->d_pacc, c->d_pden, c->d_pscale);
+      PFT_CUDA_TRY(cudaGetLastError());
+    }
     for (int col = 0; col < c->ncol; ++col) {
       a.list = c->d_sched + c->col_off[col];
       a.count = c->col_off[col + 1] - c->col_off[col];
       int rc = launch_pie(c, transform, MODE_COLOURED, a, st);
       if (rc != PFT_OK) return rc;
+      if (blind) {
+        k_probe_apply<<<1, 1024, 0, st>>>(c->d_probe, n2i, c->d_pacc, c->d_pden, (float)gamma,
+                                          (float)(c->pb.delta_rel > 0 ? c->pb.delta_rel : 1e-3), c->d_pscale);
+        PFT_CUDA_TRY(cudaGetLastError());
+      }
     }
   } else {
     PFT_CUDA_TRY(cudaMemsetAsync(c->d_acc, 0, sizeof(float2) * HW, st));
@@ -602,14 +687,15 @@ int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stat
 }
 
 // Returns the executable graph of a sweep, capturing it on first use.
-int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaGraphExec_t* out) {
+int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaGraphExec_t* out,
+                double gamma = -1.0) {
   for (auto& g : c->graphs)
-    if (g.obj == obj && g.transform == transform && g.beta == beta && g.stats == stats) {
+    if (g.obj == obj && g.transform == transform && g.beta == beta && g.stats == stats && g.gamma == gamma) {
       *out = g.exec;
       return PFT_OK;
     }
   PFT_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_sweep(c, obj, transform, beta, stats, c->cap_stream);
+  int rc = enqueue_sweep(c, obj, transform, beta, stats, c->cap_stream, gamma);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   if (rc != PFT_OK) {
@@ -625,24 +711,28 @@ int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats,
     cudaGraphExecDestroy(c->graphs.front().exec);
     c->graphs.erase(c->graphs.begin());
   }
-  c->graphs.push_back({obj, transform, beta, stats, exec});
+  c->graphs.push_back({obj, transform, beta, gamma, stats, exec});
   *out = exec;
   return PFT_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stats* stats, void* stream) {
+int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, pie_stats* stats, void* stream) {
   if (!c || !object) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
   if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
     return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
   if (transform == PIE_TRANSFORM_FULL && !c->have_full)
     return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n in {16, 32, 64, 128}, not %d", c->n);
   cudaStream_t st = (cudaStream_t)stream;
+  if (gamma >= 0.0) {
+    if (c->pb.mode != PIE_MODE_COLOURED)
+      return pfth::set_error(PFT_ERR_UNSUPPORTED, "blind PIE runs in coloured mode");
+    const size_t n2 = (size_t)c->n * c->n;
+    if (!c->d_pacc) PFT_CUDA_TRY(cudaMalloc(&c->d_pacc, sizeof(float2) * n2));
+    if (!c->d_pden) PFT_CUDA_TRY(cudaMalloc(&c->d_pden, sizeof(float) * n2));
+    if (!c->d_pscale) PFT_CUDA_TRY(cudaMalloc(&c->d_pscale, sizeof(float)));
+  }
   cudaGraphExec_t exec = nullptr;
-  int rc = sweep_graph(c, (float2*)object, transform, beta, stats != nullptr, &exec);
+  int rc = sweep_graph(c, (float2*)object, transform, beta, stats != nullptr, &exec, gamma);
   if (rc != PFT_OK) return rc;
   PFT_CUDA_TRY(cudaGraphLaunch(exec, st));
   if (stats) {
@@ -653,6 +743,44 @@ int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stat
     if (!std::isfinite(stats->phi) || !std::isfinite(stats->rel_change))
       return pfth::set_error(PFT_ERR_NONFINITE, "non-finite objective or object change");
   }
+  return PFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stats* stats, void* stream) {
+  return iterate(c, object, transform, beta, -1.0, stats, stream);
+}
+
+int pie_iteration_blind(pie_ctx* c, void* object, int transform, double beta, double gamma, pie_stats* stats,
+                        void* stream) {
+  if (!(gamma >= 0.0)) return pfth::set_error(PFT_ERR_INVALID_ARG, "need gamma >= 0");
+  return iterate(c, object, transform, beta, gamma, stats, stream);
+}
+
+int pie_ctx_probe(const pie_ctx* c, void* probe_out, void* stream) {
+  if (!c || !probe_out) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  PFT_CUDA_TRY(cudaMemcpyAsync(probe_out, c->d_probe, sizeof(float2) * c->n * c->n, cudaMemcpyDeviceToDevice,
+                               (cudaStream_t)stream));
+  return PFT_OK;
+}
+
+int pie_ctx_set_probe(pie_ctx* c, const void* probe, void* stream) {
+  if (!c || !probe) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n2 = (size_t)c->n * c->n;
+  std::vector<float2> hp(n2);
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_probe, probe, sizeof(float2) * n2, cudaMemcpyDeviceToDevice, st));
+  PFT_CUDA_TRY(cudaMemcpyAsync(hp.data(), probe, sizeof(float2) * n2, cudaMemcpyDeviceToHost, st));
+  PFT_CUDA_TRY(cudaStreamSynchronize(st));
+  float m = 0.f;
+  for (auto& v : hp) m = std::max(m, v.x * v.x + v.y * v.y);
+  if (!(m > 0.f) || !std::isfinite(m)) return pfth::set_error(PFT_ERR_NONFINITE, "probe is zero or not finite");
+  c->probe_max2 = m;
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);  // step scales depend on the probe
+  c->graphs.clear();
   return PFT_OK;
 }
 
@@ -766,7 +894,7 @@ int pie_amp_loss_grad(pie_ctx* c, const void* object, const void* probe, void* g
   PFT_CUDA_TRY(cudaMemsetAsync(grad_obj, 0, sizeof(float2) * HW, st));
   if (grad_probe) PFT_CUDA_TRY(cudaMemsetAsync(grad_probe, 0, sizeof(float2) * c->n * c->n, st));
   PFT_CUDA_TRY(cudaMemsetAsync(c->d_red, 0, sizeof(double), st));
-  PieArgs a;
+  PieArgs a = {};
   a.inst = nullptr;
   a.work = nullptr;
   a.obj = nullptr;

@@ -58,6 +58,11 @@ struct PieArgs {
   float2* acc;              // MODE_BATCHED: sum conj(w) dpsi; MODE_GRAD: grad_obj
   float2* gprobe;           // MODE_GRAD: grad_probe (may be null)
   double* red;              // red[0] += sum ||R||^2 (MODE_GRAD: the loss)
+  // blind PIE (coloured mode): a second round per position accumulates the
+  // probe step of Eq. epie_probe_update at the updated patch
+  float2* pacc;             // sum conj(z_new) dpsi' over the colour (null = non-blind)
+  float* pden;              // sum |z_new|^2 over the colour
+  const float* pscale;      // max |w|^2 of the current probe (divides coef when set)
 };
 
 template <int C>
@@ -142,7 +147,7 @@ __device__ __forceinline__ PieItem resolve(const PieArgs& a, int it) {
     r.obj_w = a.obj_w;
     r.probe = a.probe;
     r.dat = a.dat + (long long)j * DAT;
-    r.coef = a.coef;
+    r.coef = a.pscale ? a.coef / *a.pscale : a.coef;
     r.acc = a.acc;
     r.red = a.red;
     r.obase = (long long)rc.x * a.obj_w + rc.y;
@@ -165,6 +170,14 @@ __device__ __forceinline__ void apply_update(const PieArgs& a, const PieItem& p,
     atomicAdd(p.acc + oidx, cmulc(dpsi, w));
     if (a.gprobe) atomicAdd(a.gprobe + pidx, cmulc(dpsi, p.objr[oidx]));
   }
+}
+
+// Blind PIE, second round: accumulate conj(z_new) dpsi' and |z_new|^2 per probe pixel.
+__device__ __forceinline__ void accumulate_probe(const PieArgs& a, const PieItem& p, long long oidx, float2 dpsi,
+                                                 int pidx, float inv_n2) {
+  const float2 zn = p.objr[oidx];
+  atomicAdd(a.pacc + pidx, cscale(cmulc(dpsi, zn), inv_n2));
+  atomicAdd(a.pden + pidx, cabs2(zn));
 }
 
 template <int NT>
@@ -222,9 +235,11 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
   const int r0 = rank * RN;
   LaneNet<P, false> net;
   net.init(k, stw);
+  const int rounds = (MODE == MODE_COLOURED && a.pacc) ? 2 : 1;
   for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
     const PieItem p = resolve<M * M>(a, it);
     const long long obase = p.obase;
+    for (int round = 0; round < rounds; ++round) {
     // 1. rows (axis 2) of the exit wave -> column owners
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int u = r0 + u0 + g;
@@ -256,7 +271,7 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
       float2* z = sZ + (i / CM) * S::ZS + (i % CM);
       *z = residual<MODE>(*z, __ldg(dj + (i / CM) * M + (i % CM)), part);
     }
-    block_accumulate<NT>(part, sred, p.red);
+    block_accumulate<NT>(round == 0 ? part : 0.0, sred, p.red);
     __syncthreads();
     // 3c. adjoint columns -> row owners
     for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
@@ -278,9 +293,15 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
         const int v = Q * k + l;
-        apply_update<MODE>(a, p, obase + (long long)u * p.obj_w + v, __ldg(p.probe + u * N + v), xv[l], u * N + v);
+        const long long oidx = obase + (long long)u * p.obj_w + v;
+        if (round == 0)
+          apply_update<MODE>(a, p, oidx, __ldg(p.probe + u * N + v), xv[l], u * N + v);
+        else
+          accumulate_probe(a, p, oidx, xv[l], u * N + v, 1.f / (float)(N * N));
       }
     }
+    if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
+    }  // round
     if constexpr (C == 1) __syncthreads();
   }
 }
@@ -319,9 +340,11 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
   const int r0 = rank * RN, c0 = rank * CN;
   typename F::Net net;
   F::init_net(net, l, tw);
+  const int rounds = (MODE == MODE_COLOURED && a.pacc) ? 2 : 1;
   for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
     const PieItem p = resolve<N * N>(a, it);
     const long long obase = p.obase;
+    for (int round = 0; round < rounds; ++round) {
     // 1. FFT of this CTA's rows of the exit wave -> column-slot owners
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int u = r0 + u0 + g;
@@ -358,7 +381,7 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
       float2* z = sC + sa * S::SCS + sb;
       *z = residual<MODE>(*z, __ldg(dj + F::freq_of_slot(sa) * N + F::freq_of_slot(c0 + sb)), part);
     }
-    block_accumulate<NT>(part, sred, p.red);
+    block_accumulate<NT>(round == 0 ? part : 0.0, sred, p.red);
     __syncthreads();
     // 3c. adjoint FFT of the local columns -> row owners (natural row order)
     for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
@@ -384,9 +407,15 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int v = l + L * e;
-        apply_update<MODE>(a, p, obase + (long long)u * p.obj_w + v, __ldg(p.probe + u * N + v), x[e], u * N + v);
+        const long long oidx = obase + (long long)u * p.obj_w + v;
+        if (round == 0)
+          apply_update<MODE>(a, p, oidx, __ldg(p.probe + u * N + v), x[e], u * N + v);
+        else
+          accumulate_probe(a, p, oidx, x[e], u * N + v, 1.f / (float)(N * N));
       }
     }
+    if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
+    }  // round
     if constexpr (C == 1) __syncthreads();
   }
 }

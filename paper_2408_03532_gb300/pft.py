@@ -103,6 +103,9 @@ def load() -> ctypes.CDLL:
         "pie_ctx_colours": (ctypes.c_int, [_P, _P, _P]),
         "pie_ctx_info_get": (ctypes.c_int, [_P, _P]),
         "pie_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
+        "pie_iteration_blind": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P]),
+        "pie_ctx_probe": (ctypes.c_int, [_P, _P, _P]),
+        "pie_ctx_set_probe": (ctypes.c_int, [_P, _P, _P]),
         "warm_start_then_refine": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse": (ctypes.c_int, [_P, _P, _P, _P, _P]),
         "pie_tv_step": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, _P]),
@@ -332,6 +335,26 @@ class PieContext:
         if o.shape != (self.npos,):
             raise ValueError("order must be a permutation of the positions")
         _check(load().pie_ctx_set_order(self._h, o.ctypes.data))
+
+    def iteration_blind(self, obj, transform: int = TRANSFORM_FULL, beta: float = 1.0, gamma: float = 1.0,
+                        stats: bool = True, stream=None):
+        """One blind sweep (object and probe updated; coloured mode)."""
+        self._obj(obj)
+        st = PieStats()
+        _check(load().pie_iteration_blind(self._h, _ptr(obj), transform, beta, gamma,
+                                          ctypes.byref(st) if stats else None, _stream(stream)))
+        return {"phi": st.phi, "rel_change": st.rel_change} if stats else None
+
+    def probe(self, stream=None):
+        import torch
+        out = torch.empty(self.n, self.n, dtype=torch.complex64, device="cuda")
+        _check(load().pie_ctx_probe(self._h, _ptr(out), _stream(stream)))
+        return out
+
+    def set_probe(self, probe, stream=None):
+        import torch
+        _need(probe, torch.complex64, (self.n, self.n), "probe")
+        _check(load().pie_ctx_set_probe(self._h, _ptr(probe), _stream(stream)))
 
     def nrmse(self, obj, truth, stream=None) -> float:
         self._obj(obj)

@@ -240,7 +240,7 @@ def test_autograd_function_matches_oracle_and_fd(env):
     z64 = G["init"].astype(np.complex64).astype(np.complex128)
     w64 = G["probe"].astype(np.complex64).astype(np.complex128)
     lo, gzo, gwo = ograd.amplitude_loss_grad(z64, w64, G["pos"], d, T)
-    assert float(loss) == pytest.approx(lo, rel=TOL)
+    assert float(loss.detach()) == pytest.approx(lo, rel=TOL)
     assert rel(gz, gzo) < TOL and rel(gw, gwo) < TOL
     rng = np.random.default_rng(5)
     pos = G["pos"]
@@ -308,3 +308,28 @@ def test_hybrid_with_tv_matches_oracle(env, small):
         assert abs(g["nrmse"] - o["nrmse"]) < 1e-4
         assert g["rel_change"] == pytest.approx(o["change"], rel=1e-3)
     assert rel(z.cpu().numpy(), zo) < 1e-4
+
+
+@pytest.mark.parametrize("transform", ["pft", "full"])
+def test_blind_sweeps_match_oracle(env, small, transform):
+    """Blind PIE (Eq. pie_update with Eq. epie_probe_update), colour-synchronous,
+    from a perturbed probe: three sweeps of object and probe match the oracle."""
+    torch, pft = env
+    P = small
+    probe0 = P["probe"] * (1 + 0.2 * np.exp(2j * np.pi * np.random.default_rng(11).random(P["probe"].shape)))
+    probe0 = probe0.astype(np.complex64)
+    ctx = pft.PieContext(P["obj"].shape, c64(probe0, torch), P["pos"],
+                         torch.from_numpy(P["intensities"].astype(np.float32)).cuda(), M=P["M"])
+    z = c64(P["init"], torch)
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    phis = [ctx.iteration_blind(z, tr, 1.0, 0.3)["phi"] for _ in range(3)]
+    T, d = oracle_T(P, transform)
+    col = opie.greedy_colouring(P["pos"], 32, 32)
+    zo, wo = P["init"].astype(np.complex64).astype(np.complex128), probe0.astype(np.complex128)
+    for k in range(3):
+        zo, wo, phi = opie.epie_colour_sweep(zo, wo, P["pos"], d, T, 1.0, 0.3, col)
+        assert phis[k] == pytest.approx(phi, rel=1e-4)
+    assert rel(z.cpu().numpy(), zo) < 1e-4
+    assert rel(ctx.probe().cpu().numpy(), wo) < 1e-4
+    ctx.set_probe(c64(probe0, torch))
+    assert rel(ctx.probe().cpu().numpy(), probe0) == 0.0

@@ -154,3 +154,56 @@ def test_colouring_in_a_given_order():
     for x, y in zip(cm, cm[1:]):
         assert col[x] < col[y] or (col[x] == col[y] and rank[int(x)] < rank[int(y)])
     assert np.array_equal(pie.greedy_colouring(pos, 32, 32, np.arange(120)), pie.greedy_colouring(pos, 32, 32))
+
+
+def test_epie_single_position_probe_step():
+    """One position, one colour: the probe step equals Eq. epie_probe_update at
+    the updated patch with the step gamma / (|z|^2 + delta); with gamma = 0 the
+    probe is unchanged and the object step is the non-blind one."""
+    n = 16
+    obj = _rand((24, 24), 8)
+    probe = np.exp(1j * np.random.default_rng(9).random((n, n)))
+    d = np.random.default_rng(10).random((1, n, n)) + 0.1
+    pos = np.array([[3, 4]], dtype=np.int32)
+    T = pie.full_transform(n, n)
+    col = np.zeros(1, dtype=np.int64)
+    z0, w0, _ = pie.epie_colour_sweep(obj, probe, pos, d, T, 0.7, 0.0, col)
+    zs, _ = pie.pie_sweep(obj, probe, pos, d, T, 0.7)
+    assert np.allclose(z0, zs, atol=1e-14) and np.allclose(w0, probe, atol=0)
+    z1, w1, _ = pie.epie_colour_sweep(obj, probe, pos, d, T, 0.7, 0.5, col, delta_rel=0.0)
+    zj = z1[3:3 + n, 4:4 + n]
+    step = np.conj(zj) * (probe * zj - np.fft.ifft2(d[0] * np.exp(1j * np.angle(np.fft.fft2(probe * zj)))))
+    assert np.allclose(w1, probe - 0.5 * step / np.abs(zj) ** 2, atol=1e-12)
+
+
+def test_epie_fits_the_data_up_to_blind_ambiguities():
+    """Blind PIE from a perturbed probe: object and probe are only determined up
+    to the ambiguities of the blind problem (z -> a z, w -> w / a, and opposite
+    linear phase ramps), so the pin is on quantities they leave unchanged: the
+    residual Phi falls by an order of magnitude and the exit-wave moduli
+    |w . Q_j z| approach the true ones (noise-free data)."""
+    obj = synth.make_object(96)
+    probe = synth.make_probe(32)
+    pos = synth.fermat_scan(96, 32, 60)
+    d = pie.amplitudes(synth.simulate_intensities(obj, probe, pos))
+    col = pie.greedy_colouring(pos, 32, 32)
+    w = probe * (1 + 0.2 * np.exp(2j * np.pi * np.random.default_rng(11).random(probe.shape)))
+    z = synth.random_init(96)
+    T = pie.full_transform(32, 32)
+
+    def exit_err(z, w):
+        num = den = 0.0
+        for r, c in pos:
+            a = np.abs(w * z[r:r + 32, c:c + 32])
+            b = np.abs(probe * obj[r:r + 32, c:c + 32])
+            num += np.sum((a - b) ** 2)
+            den += np.sum(b ** 2)
+        return np.sqrt(num / den)
+
+    phis = []
+    e0 = exit_err(z, w)
+    for _ in range(60):
+        z, w, phi = pie.epie_colour_sweep(z, w, pos, d, T, 1.0, 0.2, col)
+        phis.append(phi)
+    assert phis[-1] < 0.1 * phis[0]
+    assert exit_err(z, w) < 0.25 * e0
