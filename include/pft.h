@@ -58,6 +58,8 @@ extern "C" {
 #define PFT_PATH_DIRECT      2   /* exact partial DFT (dense M x n per axis)     */
 
 #define PFT_PREC_FP32        0   /* FP32 CUDA-core arithmetic, FP32 accumulation */
+#define PFT_PREC_SPLIT_BF16  1   /* tensor cores: BF16 hi + lo operand splits,
+                                    three products per term, FP32 accumulation */
 
 #define PIE_TRANSFORM_PFT    0   /* PIE with the plan's partial transform (M x M) */
 #define PIE_TRANSFORM_FULL   1   /* PIE with the full n x n FFT                   */

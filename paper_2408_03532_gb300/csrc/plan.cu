@@ -329,7 +329,8 @@ int pft_plan_create(pft_plan** out, int n1, int n2, int M1, int M2, int p1, int 
   if (!(eps > 0.0 && eps < 1.0)) return pfth::set_error(PFT_ERR_INVALID_ARG, "need 0 < eps < 1");
   if (path != PFT_PATH_AUTO && path != PFT_PATH_FACTORISED && path != PFT_PATH_DIRECT)
     return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown path %d", path);
-  if (precision != PFT_PREC_FP32) return pfth::set_error(PFT_ERR_UNSUPPORTED, "precision %d not built", precision);
+  if (precision != PFT_PREC_FP32 && precision != PFT_PREC_SPLIT_BF16)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown precision %d", precision);
   if (path == PFT_PATH_DIRECT) return pfth::set_error(PFT_ERR_UNSUPPORTED, "the direct path is not built");
   if (n1 != n2 || M1 != M2 || p1 != p2 || r1 != r2)
     return pfth::set_error(PFT_ERR_UNSUPPORTED, "square frames (n1 = n2, M1 = M2, p1 = p2) are built");
@@ -342,6 +343,18 @@ int pft_plan_create(pft_plan** out, int n1, int n2, int M1, int M2, int p1, int 
   }
   p->path = PFT_PATH_FACTORISED;
   p->precision = precision;
+  if (precision == PFT_PREC_SPLIT_BF16) {
+    if (!pfth::tc_supported(p->n1, p->M1, p->p1)) {
+      pft_plan_destroy(p);
+      return pfth::set_error(PFT_ERR_UNSUPPORTED, "split-BF16 is built for n=256, M=32, p=16 (got n=%d M=%d p=%d)",
+                             n1, M1, p1 ? p1 : M1 / 2);
+    }
+    rc = pfth::tc_build_tables(p);
+    if (rc != PFT_OK) {
+      pft_plan_destroy(p);
+      return rc;
+    }
+  }
   *out = p;
   return PFT_OK;
 }
@@ -351,6 +364,8 @@ int pft_plan_destroy(pft_plan* p) {
   cudaFree(p->d_W);
   cudaFree(p->d_twp);
   cudaFree(p->d_B);
+  cudaFree(p->d_tc);
+  if (p->h_status) cudaFreeHost(p->h_status);
   delete p;
   return PFT_OK;
 }
@@ -386,6 +401,14 @@ int pft_plan_tables(const pft_plan* p, int axis, float* B, float* W) {
 }
 
 int pft_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void* stream) {
+  if (plan && plan->precision == PFT_PREC_SPLIT_BF16) {
+    if ((!x || !y) && batch) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+    if (batch < 0) return pfth::set_error(PFT_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return PFT_OK;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
+      return pfth::set_error(PFT_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
+    return pfth::tc_forward(plan, x, y, batch, stream);
+  }
   return launch_frames(plan, x, y, batch, stream, false);
 }
 

@@ -12,6 +12,9 @@ struct pft_plan {
   float2* d_twp = nullptr;  // [16] : e^{-2 pi i m / p}, m < p/2
   float* d_B = nullptr;     // [2][q][RMAX] full B table (inspection only)
   int kid = -1;             // index in the frame-kernel registry
+  void* d_tc = nullptr;     // split-BF16 tensor-core table (MMA operand layout)
+  int* h_status = nullptr;  // device-side wait status (mapped host word)
+  int* d_status = nullptr;
 };
 
 namespace pfth {
@@ -29,5 +32,10 @@ int find_frame_kernels(int P, int Q, int MP);
 
 // Builds a square plan's tables; used by pft_plan_create and the PIE context.
 int build_plan(pft_plan* p, int n, int M, int P, double eps, int r_force);
+
+// Split-BF16 tensor-core path (pft_tc.cu).
+bool tc_supported(int n, int M, int p);
+int tc_build_tables(pft_plan* plan);
+int tc_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void* stream);
 
 }  // namespace pfth

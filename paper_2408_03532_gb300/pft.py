@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "pft.h")
 PFT_OK = 0
 PATH_AUTO, PATH_FACTORISED, PATH_DIRECT = 0, 1, 2
 PREC_FP32 = 0
+PREC_SPLIT_BF16 = 1
 TRANSFORM_PFT, TRANSFORM_FULL = 0, 1
 MODE_COLOURED, MODE_BATCHED = 0, 1
 _ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "OOM"}
