@@ -237,6 +237,9 @@ def main() -> None:
     ap.add_argument("--no-pft-batch", action="store_true")
     ap.add_argument("--pft-frames", type=int, default=4096)
     ap.add_argument("--no-batch64", action="store_true")
+    ap.add_argument("--only-pft-batch", action="store_true",
+                    help="run only the standalone batched transform (--pft-frames frames) and print its JSON; "
+                         "not a benchmark line (used as a small profiling target)")
     args = ap.parse_args()
     rank, world, local = dist_env()
 
@@ -256,6 +259,11 @@ def main() -> None:
     from paper_2408_03532_gb300 import pft, synth
     libbuild.build()
     pft.load()
+
+    if args.only_pft_batch:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps(measure_pft_batch(pft, torch, dev, torch.cuda.current_stream(dev), flush, args.pft_frames)))
+        return
 
     mode = pft.MODE_COLOURED if args.mode == "coloured" else pft.MODE_BATCHED
     P = synth.spiral_problem()
@@ -424,10 +432,49 @@ def measure_pft_batch(pft, torch, dev, stream, flush, frames: int = 4096, n: int
                         "adjoint_ms": ad, "adjoint_gbs": byts / ad / 1e6, "adjoint_frac": byts / ad / 1e6 / peak,
                         "fft_crop_ms": fc, "fft_crop_gbs": byts / fc / 1e6, "pft_speedup_vs_fft_crop": fc / f,
                         "frames_per_s_forward": frames / (f / 1e3)}
+        if M == 32:
+            out["M32"]["split_bf16"] = measure_split_bf16(pft, torch, plan, x, y, timed, byts, peak, kind, f, fc)
         del y, xa, plan
     del x
     torch.cuda.empty_cache()
     return out
+
+
+# DRAM traffic of k_pft_tc_fwd from one ncu capture (512 frames of 256 x 256,
+# M = 32; read + write bytes per frame), valid for the source it was taken on.
+TC_TRAFFIC = {"source_sha256": "1bafaebe3c7ed6752741b36ab756937a72c5c37931542666746c2ad5ef4e112a",
+              "bytes_per_frame": (268574208 + 3338752) / 512}
+
+
+def _tc_source_sha() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2408_03532_gb300", "csrc", "pft_tc.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+
+
+def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32_ms, fft_crop_ms) -> dict:
+    """The split-BF16 tensor-core forward (tcgen05) on the same frames: time,
+    HBM roofline against the measured copy bandwidth, and its largest per-frame
+    relative difference from the FP32 CUDA-core PFT."""
+    frames = x.shape[0]
+    tc = pft.Plan(x.shape[-1], 32, precision=pft.PREC_SPLIT_BF16)
+    y = torch.empty_like(y32)
+    ms = timed(lambda: tc.forward(x, out=y))
+    plan32.forward(x, out=y32)
+    torch.cuda.synchronize()
+    diff = torch.linalg.vector_norm((y - y32).reshape(frames, -1), dim=1)
+    rel = float((diff / torch.linalg.vector_norm(y32.reshape(frames, -1), dim=1)).max())
+    achieved = byts / ms / 1e6
+    traffic = None
+    if TC_TRAFFIC["bytes_per_frame"] and TC_TRAFFIC["source_sha256"] == _tc_source_sha():
+        traffic = TC_TRAFFIC["bytes_per_frame"] * frames
+    del y, tc
+    return {"forward_ms": ms, "forward_gbs": achieved, "frames_per_s_forward": frames / (ms / 1e3),
+            "speedup_vs_fp32": fp32_ms / ms, "speedup_vs_fft_crop": fft_crop_ms / ms,
+            "max_rel_diff_vs_fp32": rel,
+            "roofline": {"bound": "hbm", "kernel": "k_pft_tc_fwd", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": kind,
+                         "algorithmic_bytes": byts, "traffic": traffic}}
 
 
 def measure_batch64(pft, synth, torch, dev, stream, flush, reps: int = 3) -> dict:

@@ -53,7 +53,8 @@ constexpr int kR = 128 / kF;            // rows per frame in one row tile
 constexpr int kTiles = kN / kR;         // row tiles per group
 constexpr int kC = 32;                  // K columns per X stage
 constexpr int kChunks = kN / kC;        // X stages per row tile
-constexpr int kStages = 2;
+constexpr int kStages = 4;
+constexpr int kA2 = 1;                  // column-pass operand buffers
 constexpr int kTabRows = 4 * kM;        // A_re hi, A_im hi, A_re lo, A_im lo
 constexpr uint32_t CM = 128;            // bytes of one 8 x 16-byte core matrix
 constexpr uint32_t TAB_LBO = (kTabRows / 8) * CM;        // 2048
@@ -63,12 +64,12 @@ constexpr uint32_t X_LBO = 16 * CM + 32;                 // padded: conflict-fre
 constexpr uint32_t X_COMP = (kC / 8) * X_LBO;
 constexpr uint32_t X_STAGE = 4 * X_COMP;
 constexpr uint32_t A2_LBO = 16 * CM + 32;
-constexpr uint32_t A2_COMP = (kR / 8) * A2_LBO;
+constexpr uint32_t A2_COMP = (kR / 8) * A2_LBO + 16;  // +16: hi / lo words on different banks
 constexpr uint32_t A2_STAGE = 4 * A2_COMP;
 constexpr uint32_t OFF_TAB = 0;
 constexpr uint32_t OFF_X = OFF_TAB + TAB_BYTES;
 constexpr uint32_t OFF_A2 = OFF_X + kStages * X_STAGE;
-constexpr uint32_t OFF_BAR = OFF_A2 + 2 * A2_STAGE;
+constexpr uint32_t OFF_BAR = OFF_A2 + kA2 * A2_STAGE;
 constexpr int NBAR = 2 * kStages + 8 + 3;
 constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * NBAR;
 constexpr uint32_t OFF_ABORT = OFF_SLOT + 8;
@@ -76,7 +77,7 @@ constexpr uint32_t SMEM_USED = OFF_ABORT + 8;
 // The full opt-in shared memory is requested: every descriptor read then stays
 // inside the CTA's allocation even under the other reading of LBO and SBO.
 constexpr uint32_t SMEM_BYTES = 232448;
-static_assert(SMEM_USED + 1024 <= SMEM_BYTES, "shared memory layout too large");
+static_assert(SMEM_USED <= SMEM_BYTES, "shared memory layout too large");
 
 constexpr int kEpiWarps = 4, kMmaWarp = 4, kCvtWarp0 = 8, kCvtWarps = 16;  // warps 5-7 idle
 constexpr int kThreadsTC = 32 * (kCvtWarp0 + kCvtWarps);
@@ -89,6 +90,7 @@ constexpr int kDepth = 3;  // X stages held in registers per loader thread (2 in
 
 static_assert(kF * kR == 128 && kTiles * kR == kN && kChunks * kC == kN, "tiling");
 static_assert(COL_ACC + ACC_COLS <= TMEM_COLS, "tensor memory");
+static_assert(kA2 == 1 || kA2 == 2, "column-pass operand buffers");
 
 __device__ __forceinline__ void split_store(uint8_t* base, uint32_t comp_bytes, uint32_t off, float a, float b) {
   const __nv_bfloat162 hi = __floats2bfloat162_rn(a, b);
@@ -98,18 +100,23 @@ __device__ __forceinline__ void split_store(uint8_t* base, uint32_t comp_bytes, 
   *reinterpret_cast<__nv_bfloat162*>(base + comp_bytes + off) = lo;
 }
 
-__device__ __forceinline__ void split_store1(uint8_t* base, uint32_t comp_bytes, uint32_t off, float v) {
+// Splits v into BF16 hi + lo; the lane pair (2r, 2r+1) exchanges its parts so
+// that the even lane writes (hi_2r, hi_2r+1) and the odd lane (lo_2r, lo_2r+1)
+// at `off` (the odd lane's `off` already points into the lo component).
+__device__ __forceinline__ void pair_store(uint8_t* base, uint32_t off, float v, bool odd) {
   const __nv_bfloat16 hi = __float2bfloat16_rn(v);
   const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-  *reinterpret_cast<__nv_bfloat16*>(base + off) = hi;
-  *reinterpret_cast<__nv_bfloat16*>(base + comp_bytes + off) = lo;
+  const uint32_t mine = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
+  const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
+  const uint32_t word = odd ? ((other >> 16) | (mine & 0xFFFF0000u)) : ((mine & 0xFFFFu) | (other << 16));
+  *reinterpret_cast<uint32_t*>(base + off) = word;
 }
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_pft_tc_fwd(const float2* __restrict__ x, float2* __restrict__ y, long long batch,
                  const uint4* __restrict__ tab, int* status) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t* sm = smem_raw;  // no-swizzle operands need 16-byte alignment only
   const uint32_t sb = smem_u32(sm);
   const uint32_t bar = sb + OFF_BAR;
   const uint32_t X_FULL = bar, X_EMPTY = bar + 8 * kStages, ACC_FULL = bar + 16 * kStages,
@@ -158,8 +165,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       bool ok = true;
       auto col_pass = [&](long long Tp) -> bool {
         const int ip = (int)(Tp % kTiles);
-        const int b = (int)(Tp & 1);
-        const uint32_t v = (uint32_t)(Tp >> 1);
+        const int b = (int)(Tp % kA2);
+        const uint32_t v = (uint32_t)(Tp / kA2);
         if (ip == 0 && !mbar_wait(COL_EMPTY, ((uint32_t)(Tp / kTiles) & 1u) ^ 1u, abort_flag, kWaitNs)) return false;
         if (!mbar_wait(A2_FULL + 8 * b, v & 1u, abort_flag, kWaitNs)) return false;
         tc_fence_after();
@@ -238,18 +245,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // ------------------------------------------------------------- epilogue
     const int q = warp;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const uint32_t kofs = (uint32_t)(lane >> 3) * A2_LBO + (uint32_t)(lane & 7) * 2;
+    // Lanes 2r and 2r+1 hold K-adjacent rows: the even lane stores both hi
+    // parts, the odd lane both lo parts, as one 32-bit word each.
+    const bool odd = lane & 1;
+    const uint32_t kofs = (uint32_t)(lane >> 3) * A2_LBO + (uint32_t)((lane & 7) >> 1) * 4 + (odd ? A2_COMP : 0u);
     long long T = 0;
     for (long long it = 0; it < nloc; ++it) {
       const long long g = blockIdx.x + it * gridDim.x;
       for (int i = 0; i < kTiles; ++i, ++T) {
         const int b = (int)(T & 1);
         const uint32_t v = (uint32_t)(T >> 1);
+        const int ba = (int)(T % kA2);
+        const uint32_t va = (uint32_t)(T / kA2);
         if (!mbar_wait(ACC_FULL + 8 * b, v & 1u, abort_flag, kWaitNs)) goto epi_done;
-        if (!mbar_wait(A2_EMPTY + 8 * b, (v & 1u) ^ 1u, abort_flag, kWaitNs)) goto epi_done;
+        if (!mbar_wait(A2_EMPTY + 8 * ba, (va & 1u) ^ 1u, abort_flag, kWaitNs)) goto epi_done;
         tc_fence_after();
         {
-          uint8_t* a2 = sm + OFF_A2 + b * A2_STAGE;
+          uint8_t* a2 = sm + OFF_A2 + ba * A2_STAGE;
           const uint32_t z1 = tmem + lane_off + b * ACC_COLS, z2 = z1 + 2 * kM;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -260,7 +272,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               const uint32_t m2 = (uint32_t)(q * kM + 16 * h + t);
-              split_store1(a2, A2_COMP, kofs + (m2 >> 3) * CM + (m2 & 7) * 16, p0[t] - p1[t]);
+              pair_store(a2, kofs + (m2 >> 3) * CM + (m2 & 7) * 16, p0[t] - p1[t], odd);
             }
             tmem_ld16(z1 + kM + 16 * h, p0);
             tmem_ld16(z2 + 16 * h, p1);
@@ -268,7 +280,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               const uint32_t m2 = (uint32_t)(q * kM + 16 * h + t);
-              split_store1(a2 + 2 * A2_COMP, A2_COMP, kofs + (m2 >> 3) * CM + (m2 & 7) * 16, p0[t] + p1[t]);
+              pair_store(a2 + 2 * A2_COMP, kofs + (m2 >> 3) * CM + (m2 & 7) * 16, p0[t] + p1[t], odd);
             }
           }
         }
@@ -277,7 +289,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(ACC_EMPTY + 8 * b);
-          mbar_arrive(A2_FULL + 8 * b);
+          mbar_arrive(A2_FULL + 8 * ba);
         }
         if (i == kTiles - 1) {
           if (!mbar_wait(COL_FULL, (uint32_t)(it & 1), abort_flag, kWaitNs)) goto epi_done;
@@ -352,13 +364,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
       load(L + kDepth, r);
       return true;
     };
-    static_assert(kDepth == 3, "the loop below is unrolled for three register stages");
-    Buf b0, b1, b2;
+    static_assert(kDepth == 3 || kDepth == 4, "the loop below is unrolled for three or four register stages");
+    Buf b0, b1, b2, b3;
     load(0, b0);
     load(1, b1);
     load(2, b2);
+    if constexpr (kDepth == 4) load(3, b3);
     for (long long L = 0; L < total; L += kDepth) {
       if (!step(L, b0) || !step(L + 1, b1) || !step(L + 2, b2)) break;
+      if constexpr (kDepth == 4) {
+        if (!step(L + 3, b3)) break;
+      }
     }
   }
 
