@@ -237,6 +237,9 @@ def main() -> None:
     ap.add_argument("--no-pft-batch", action="store_true")
     ap.add_argument("--pft-frames", type=int, default=4096)
     ap.add_argument("--no-batch64", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the built-in cluster-size heuristic instead of timing each size (for profilers, "
+                         "whose per-launch overhead distorts the autotuner's timings)")
     ap.add_argument("--only-pft-batch", action="store_true",
                     help="run only the standalone batched transform (--pft-frames frames) and print its JSON; "
                          "not a benchmark line (used as a small profiling target)")
@@ -273,7 +276,7 @@ def main() -> None:
     inten = torch.from_numpy(P["intensities"].astype(np.float32)).to(dev)
     truth = torch.from_numpy(P["obj"].astype(np.complex64)).to(dev)
     init = torch.from_numpy(P["init"].astype(np.complex64)).to(dev)
-    ctx = pft.PieContext((H, W), probe, P["pos"], inten, M=M, mode=mode)
+    ctx = pft.PieContext((H, W), probe, P["pos"], inten, M=M, mode=mode, autotune=not args.no_autotune)
     del inten
     ncol = int(ctx.colours().max()) + 1
     tuning = ctx.info()

@@ -41,6 +41,7 @@
 #include "coeffs.h"
 #include "plan.cuh"
 #include "tc.cuh"
+#include "tc_table.cuh"
 
 namespace {
 
@@ -397,35 +398,18 @@ __global__ void k_tc_table(int p, int q, int r, const double* __restrict__ a, ui
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= kM * kN) return;
   const int ti = id / kN, v = id % kN;
-  const long long t = (long long)ti - kM / 2;
-  const int kb = v / q, l = v % q;
-  double sr = 0.0, si = 0.0;
-  for (int j = 0; j < r; ++j) {
-    const double wmag = (j == 0) ? 1.0 : pow((double)t / (double)p, (double)j);
-    const double bval = a[j] * ((j == 0) ? 1.0 : pow((double)(q - 2 * l) / (double)q, (double)j));
-    long long m = ((long long)j * (p / 2) - t) % (2LL * p);
-    if (m < 0) m += 2LL * p;
-    double s, c;
-    sincospi((double)m / (double)p, &s, &c);
-    sr += wmag * bval * c;
-    si += wmag * bval * s;
-  }
-  long long mm = (t * kb) % p;
-  if (mm < 0) mm += p;
-  double s, c;
-  sincospi(-2.0 * (double)mm / (double)p, &s, &c);
-  const double ar = sr * c - si * s, ai = sr * s + si * c;
-  auto put = [&](int row, double val) {
-    const __nv_bfloat16 hi = __float2bfloat16_rn((float)val);
-    const __nv_bfloat16 lo = __float2bfloat16_rn((float)(val - (double)__bfloat162float(hi)));
-    auto at = [&](int rr) {
-      return ((uint32_t)(v / 8) * TAB_LBO + (uint32_t)(rr / 8) * CM + (uint32_t)(rr % 8) * 16 + (uint32_t)(v % 8) * 2) / 2;
-    };
-    tab[at(row)] = __bfloat16_as_ushort(hi);
-    tab[at(row + 2 * kM)] = __bfloat16_as_ushort(lo);
+  double ar, ai;
+  operator_entry(kM, p, q, r, a, ti, v, ar, ai);
+  auto at = [&](int rr) {
+    return ((uint32_t)(v / 8) * TAB_LBO + (uint32_t)(rr / 8) * CM + (uint32_t)(rr % 8) * 16 + (uint32_t)(v % 8) * 2) / 2;
   };
-  put(ti, ar);
-  put(kM + ti, ai);
+  uint16_t hi, lo;
+  split_bf16(ar, hi, lo);
+  tab[at(ti)] = hi;
+  tab[at(ti + 2 * kM)] = lo;
+  split_bf16(ai, hi, lo);
+  tab[at(kM + ti)] = hi;
+  tab[at(3 * kM + ti)] = lo;
 }
 
 }  // namespace
@@ -446,6 +430,8 @@ int tc_build_tables(pft_plan* plan) {
   k_tc_table<<<(kM * kN + 127) / 128, 128>>>(plan->p1, plan->q1, plan->r1, d_a,
                                              reinterpret_cast<uint16_t*>(plan->d_tc));
   PFT_CUDA_TRY(cudaGetLastError());
+  int rc = tc_build_adjoint_table(plan, d_a);
+  if (rc != PFT_OK) return rc;
   PFT_CUDA_TRY(cudaDeviceSynchronize());
   PFT_CUDA_TRY(cudaFree(d_a));
   PFT_CUDA_TRY(cudaHostAlloc(&plan->h_status, sizeof(int), cudaHostAllocMapped));

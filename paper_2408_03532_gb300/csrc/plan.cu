@@ -365,6 +365,7 @@ int pft_plan_destroy(pft_plan* p) {
   cudaFree(p->d_twp);
   cudaFree(p->d_B);
   cudaFree(p->d_tc);
+  cudaFree(p->d_tc_adj);
   if (p->h_status) cudaFreeHost(p->h_status);
   delete p;
   return PFT_OK;
@@ -413,6 +414,14 @@ int pft_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, voi
 }
 
 int pft_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void* stream) {
+  if (plan && plan->precision == PFT_PREC_SPLIT_BF16) {
+    if ((!x || !y) && batch) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+    if (batch < 0) return pfth::set_error(PFT_ERR_INVALID_ARG, "batch < 0");
+    if (batch == 0) return PFT_OK;
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
+      return pfth::set_error(PFT_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
+    return pfth::tc_adjoint(plan, y, x, batch, stream);
+  }
   return launch_frames(plan, y, x, batch, stream, true);
 }
 

@@ -13,6 +13,7 @@ struct pft_plan {
   float* d_B = nullptr;     // [2][q][RMAX] full B table (inspection only)
   int kid = -1;             // index in the frame-kernel registry
   void* d_tc = nullptr;     // split-BF16 tensor-core table (MMA operand layout)
+  void* d_tc_adj = nullptr; // its adjoint table conj(A)^T
   int* h_status = nullptr;  // device-side wait status (mapped host word)
   int* d_status = nullptr;
 };
@@ -37,5 +38,7 @@ int build_plan(pft_plan* p, int n, int M, int P, double eps, int r_force);
 bool tc_supported(int n, int M, int p);
 int tc_build_tables(pft_plan* plan);
 int tc_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void* stream);
+int tc_build_adjoint_table(pft_plan* plan, const double* d_a);
+int tc_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void* stream);
 
 }  // namespace pfth

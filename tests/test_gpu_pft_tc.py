@@ -1,5 +1,5 @@
-"""GPU parity of the split-BF16 tensor-core PFT (256 x 256 frames, M = 32)
-against the FP64 oracle.
+"""GPU parity of the split-BF16 tensor-core PFT and its adjoint (256 x 256
+frames, M = 32) against the FP64 oracle.
 
 Tolerance: every operand is split into BF16 hi + lo (|v - hi - lo| <= 2^-17 |v|)
 and each product is formed from three partial products, so a product carries
@@ -99,6 +99,45 @@ def test_repeat_calls_are_identical(env):
     assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("batch", [1, 2, 5])
+def test_adjoint_matches_oracle(env, oracle_plans, batch):
+    torch, pft = env
+    yv = synth.random_frames(batch, M, seed=60 + batch)
+    plan = pft.Plan(N, M, precision=pft.PREC_SPLIT_BF16)
+    x = plan.adjoint(torch.from_numpy(yv).cuda()).cpu().numpy()
+    ref = opft.pft2_adjoint(yv.astype(np.complex128), *oracle_plans)
+    err = rel_frames(x, ref)
+    assert err.max() < TOL, err
+
+
+def test_adjoint_identity_split_pair(env):
+    """<A x, y> = <x, A^H y> for the split-BF16 forward / adjoint pair, to the
+    split's accuracy."""
+    torch, pft = env
+    plan = pft.Plan(N, M, precision=pft.PREC_SPLIT_BF16)
+    x = synth.random_frames(4, N, seed=21)
+    yv = synth.random_frames(4, M, seed=22)
+    Ax = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.complex128)
+    Ahy = plan.adjoint(torch.from_numpy(yv).cuda()).cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(yv.astype(np.complex128), Ax)
+    rhs = np.vdot(Ahy, x.astype(np.complex128))
+    assert abs(lhs - rhs) <= 2 * TOL * np.linalg.norm(Ax) * np.linalg.norm(yv)
+
+
+def test_adjoint_matches_fp32_path_at_full_size(env, oracle_plans):
+    torch, pft = env
+    B = 4096
+    yv = torch.randn(B, M, M, dtype=torch.complex64, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    x_tc = pft.Plan(N, M, precision=pft.PREC_SPLIT_BF16).adjoint(yv)
+    x_32 = pft.Plan(N, M).adjoint(yv)
+    torch.cuda.synchronize()
+    d = torch.linalg.vector_norm((x_tc - x_32).reshape(B, -1), dim=1) / torch.linalg.vector_norm(x_32.reshape(B, -1), dim=1)
+    assert float(d.max()) < 2 * TOL
+    for f in (0, 151, 152, 4095):
+        ref = opft.pft2_adjoint(yv[f].cpu().numpy().astype(np.complex128)[None], *oracle_plans)
+        assert rel_frames(x_tc[f].cpu().numpy()[None], ref)[0] < TOL
+
+
 def test_unsupported_shapes_and_empty(env):
     torch, pft = env
     for n, m in [(128, 32), (256, 64), (64, 32)]:
@@ -108,3 +147,4 @@ def test_unsupported_shapes_and_empty(env):
     plan = pft.Plan(N, M, precision=pft.PREC_SPLIT_BF16)
     empty = torch.empty(0, N, N, dtype=torch.complex64, device="cuda")
     assert plan.forward(empty).shape == (0, M, M)
+    assert plan.adjoint(torch.empty(0, M, M, dtype=torch.complex64, device="cuda")).shape == (0, N, N)
