@@ -436,48 +436,74 @@ def measure_pft_batch(pft, torch, dev, stream, flush, frames: int = 4096, n: int
                         "fft_crop_ms": fc, "fft_crop_gbs": byts / fc / 1e6, "pft_speedup_vs_fft_crop": fc / f,
                         "frames_per_s_forward": frames / (f / 1e3)}
         if M == 32:
-            out["M32"]["split_bf16"] = measure_split_bf16(pft, torch, plan, x, y, timed, byts, peak, kind, f, fc)
+            out["M32"]["split_bf16"] = measure_split_bf16(pft, torch, plan, x, y, timed, byts, peak, kind, f, ad, fc)
         del y, xa, plan
     del x
     torch.cuda.empty_cache()
     return out
 
 
-# DRAM traffic of k_pft_tc_fwd from one ncu capture (512 frames of 256 x 256,
-# M = 32; read + write bytes per frame), valid for the source it was taken on.
-TC_TRAFFIC = {"source_sha256": "1bafaebe3c7ed6752741b36ab756937a72c5c37931542666746c2ad5ef4e112a",
-              "bytes_per_frame": (268574208 + 3338752) / 512}
+# DRAM traffic (read + write bytes per frame) of the split-BF16 kernels from
+# ncu captures, each valid only for the source file it was taken on.
+TC_TRAFFIC = {
+    # 4096 frames of 256 x 256, M = 32; median of 6 / 7 launches (one ncu pass each)
+    "k_pft_tc_fwd": {"source": "pft_tc.cu", "source_sha256": "e013619d75cb25739010e0d00ea07d0c9d34d37060fc6ac0de7378992fd6419a",
+                     "bytes_per_frame": (2147638016 + 30002432) / 4096},
+    "k_pft_tc_adj": {"source": "pft_tc_adj.cu", "source_sha256": "e3d99338b748ea0a4d4b0ce7b38083d91766084346370a63963eba7c5346de3e",
+                     "bytes_per_frame": (33714944 + 2082775552) / 4096},
+}
 
 
-def _tc_source_sha() -> str:
+def _csrc_sha(name: str) -> str:
     import hashlib
-    path = os.path.join(ROOT, "paper_2408_03532_gb300", "csrc", "pft_tc.cu")
+    path = os.path.join(ROOT, "paper_2408_03532_gb300", "csrc", name)
     return hashlib.sha256(open(path, "rb").read()).hexdigest()
 
 
-def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32_ms, fft_crop_ms) -> dict:
-    """The split-BF16 tensor-core forward (tcgen05) on the same frames: time,
-    HBM roofline against the measured copy bandwidth, and its largest per-frame
-    relative difference from the FP32 CUDA-core PFT."""
+def _traffic(kernel: str, frames: int):
+    rec = TC_TRAFFIC[kernel]
+    if rec["bytes_per_frame"] and rec["source_sha256"] == _csrc_sha(rec["source"]):
+        return rec["bytes_per_frame"] * frames
+    return None
+
+
+def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32_fwd_ms, fp32_adj_ms,
+                       fft_crop_ms) -> dict:
+    """The split-BF16 tensor-core forward and adjoint (tcgen05) on the same
+    frames: times, HBM rooflines against the measured copy bandwidth, and the
+    largest per-frame relative difference from the FP32 CUDA-core PFT."""
     frames = x.shape[0]
     tc = pft.Plan(x.shape[-1], 32, precision=pft.PREC_SPLIT_BF16)
     y = torch.empty_like(y32)
-    ms = timed(lambda: tc.forward(x, out=y))
+    xa = torch.empty_like(x)
+    f_ms = timed(lambda: tc.forward(x, out=y))
+    a_ms = timed(lambda: tc.adjoint(y, out=xa))
+
+    def rel(a, b):
+        d = torch.linalg.vector_norm((a - b).reshape(frames, -1), dim=1)
+        return float((d / torch.linalg.vector_norm(b.reshape(frames, -1), dim=1)).max())
+
     plan32.forward(x, out=y32)
     torch.cuda.synchronize()
-    diff = torch.linalg.vector_norm((y - y32).reshape(frames, -1), dim=1)
-    rel = float((diff / torch.linalg.vector_norm(y32.reshape(frames, -1), dim=1)).max())
-    achieved = byts / ms / 1e6
-    traffic = None
-    if TC_TRAFFIC["bytes_per_frame"] and TC_TRAFFIC["source_sha256"] == _tc_source_sha():
-        traffic = TC_TRAFFIC["bytes_per_frame"] * frames
-    del y, tc
-    return {"forward_ms": ms, "forward_gbs": achieved, "frames_per_s_forward": frames / (ms / 1e3),
-            "speedup_vs_fp32": fp32_ms / ms, "speedup_vs_fft_crop": fft_crop_ms / ms,
-            "max_rel_diff_vs_fp32": rel,
-            "roofline": {"bound": "hbm", "kernel": "k_pft_tc_fwd", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": kind,
-                         "algorithmic_bytes": byts, "traffic": traffic}}
+    rel_f = rel(y, y32)
+    x32 = plan32.adjoint(y32)
+    tc.adjoint(y32, out=xa)
+    torch.cuda.synchronize()
+    rel_a = rel(xa, x32)
+    del x32, xa, y, tc
+
+    def roof(kernel, ms):
+        achieved = byts / ms / 1e6
+        return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes": byts,
+                "traffic": _traffic(kernel, frames)}
+
+    return {"forward_ms": f_ms, "forward_gbs": byts / f_ms / 1e6, "frames_per_s_forward": frames / (f_ms / 1e3),
+            "adjoint_ms": a_ms, "adjoint_gbs": byts / a_ms / 1e6,
+            "speedup_vs_fp32": {"forward": fp32_fwd_ms / f_ms, "adjoint": fp32_adj_ms / a_ms},
+            "speedup_vs_fft_crop": fft_crop_ms / f_ms,
+            "max_rel_diff_vs_fp32": {"forward": rel_f, "adjoint": rel_a},
+            "roofline": {"forward": roof("k_pft_tc_fwd", f_ms), "adjoint": roof("k_pft_tc_adj", a_ms)}}
 
 
 def measure_batch64(pft, synth, torch, dev, stream, flush, reps: int = 3) -> dict:
