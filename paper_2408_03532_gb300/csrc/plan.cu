@@ -1,5 +1,6 @@
 // PFT plans (Algorithm 4) and the batched forward / adjoint transforms
 // (Algorithm 5 and its exact adjoint) on sm_103a.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -247,7 +248,8 @@ int build_plan(pft_plan* p, int n, int M, int P, double eps, int r_force) {
     return set_error(PFT_ERR_UNSUPPORTED, "r=%d > %d terms (eps=%g, m~/p=%g): use a larger p", r, RMAX, eps,
                      (M / 2.0) / P);
   const int kid = find_frame_kernels(P, Q, M / P);
-  if (kid < 0) return set_error(PFT_ERR_UNSUPPORTED, "no kernel built for n=%d M=%d p=%d", n, M, P);
+  if (kid < 0 && !lf_supported(n, M, P))
+    return set_error(PFT_ERR_UNSUPPORTED, "no kernel built for n=%d M=%d p=%d", n, M, P);
   double xi = 0.0, a[pftc::kMaxTerms] = {0};
   if (!pftc::design(eps, r, &xi, a, nullptr))
     return set_error(PFT_ERR_INVALID_ARG, "coefficient design failed (eps=%g r=%d)", eps, r);
@@ -265,7 +267,7 @@ int build_plan(pft_plan* p, int n, int M, int P, double eps, int r_force) {
   float* d_B1 = nullptr;
   PFT_CUDA_TRY(cudaMalloc(&d_a, sizeof(double) * pftc::kMaxTerms));
   PFT_CUDA_TRY(cudaMalloc(&p->d_W, sizeof(float2) * 2 * RMAX * M));
-  PFT_CUDA_TRY(cudaMalloc(&p->d_twp, sizeof(float2) * 16));
+  PFT_CUDA_TRY(cudaMalloc(&p->d_twp, sizeof(float2) * std::max(16, P / 2)));
   PFT_CUDA_TRY(cudaMalloc(&p->d_B, sizeof(float) * 2 * Q * RMAX));
   PFT_CUDA_TRY(cudaMemcpy(d_a, a, sizeof(double) * r, cudaMemcpyHostToDevice));
   const int total = Q * RMAX + RMAX * M + P / 2;
@@ -279,9 +281,11 @@ int build_plan(pft_plan* p, int n, int M, int P, double eps, int r_force) {
   PFT_CUDA_TRY(cudaMemcpy(hB.data(), p->d_B, sizeof(float) * Q * RMAX, cudaMemcpyDeviceToHost));
   PFT_CUDA_TRY(cudaFree(d_a));
   std::memset(&p->cst, 0, sizeof(p->cst));
-  for (int ax = 0; ax < 2; ++ax)
-    for (int l = 0; l <= Q / 2; ++l)
-      for (int j = 0; j < RMAX; ++j) p->cst.bh[ax][l][j] = hB[l * RMAX + j];
+  // the frame kernels keep rows 0 .. q/2 of B as constants (q <= 32)
+  if (Q / 2 < (int)(sizeof(p->cst.bh[0]) / sizeof(p->cst.bh[0][0])))
+    for (int ax = 0; ax < 2; ++ax)
+      for (int l = 0; l <= Q / 2; ++l)
+        for (int j = 0; j < RMAX; ++j) p->cst.bh[ax][l][j] = hB[l * RMAX + j];
   return PFT_OK;
 }
 
@@ -343,6 +347,20 @@ int pft_plan_create(pft_plan** out, int n1, int n2, int M1, int M2, int p1, int 
   }
   p->path = PFT_PATH_FACTORISED;
   p->precision = precision;
+  if (p->kid < 0) {  // large frames: split-BF16 stage A on tensor cores
+    if (precision != PFT_PREC_SPLIT_BF16) {
+      pft_plan_destroy(p);
+      return pfth::set_error(PFT_ERR_UNSUPPORTED, "n=%d frames are built for PFT_PREC_SPLIT_BF16 only", n1);
+    }
+    p->lf = true;
+    rc = pfth::lf_build(p);
+    if (rc != PFT_OK) {
+      pft_plan_destroy(p);
+      return rc;
+    }
+    *out = p;
+    return PFT_OK;
+  }
   if (precision == PFT_PREC_SPLIT_BF16) {
     if (!pfth::tc_supported(p->n1, p->M1, p->p1)) {
       pft_plan_destroy(p);
@@ -366,6 +384,7 @@ int pft_plan_destroy(pft_plan* p) {
   cudaFree(p->d_B);
   cudaFree(p->d_tc);
   cudaFree(p->d_tc_adj);
+  cudaFree(p->d_ws);
   if (p->h_status) cudaFreeHost(p->h_status);
   delete p;
   return PFT_OK;
@@ -408,6 +427,7 @@ int pft_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, voi
     if (batch == 0) return PFT_OK;
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
       return pfth::set_error(PFT_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
+    if (plan->lf) return pfth::lf_forward(plan, x, y, batch, stream);
     return pfth::tc_forward(plan, x, y, batch, stream);
   }
   return launch_frames(plan, x, y, batch, stream, false);
@@ -420,6 +440,7 @@ int pft_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, voi
     if (batch == 0) return PFT_OK;
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
       return pfth::set_error(PFT_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
+    if (plan->lf) return pfth::set_error(PFT_ERR_UNSUPPORTED, "the large-frame adjoint is not built");
     return pfth::tc_adjoint(plan, y, x, batch, stream);
   }
   return launch_frames(plan, y, x, batch, stream, true);

@@ -16,6 +16,9 @@ struct pft_plan {
   void* d_tc_adj = nullptr; // its adjoint table conj(A)^T
   int* h_status = nullptr;  // device-side wait status (mapped host word)
   int* d_status = nullptr;
+  bool lf = false;          // large-frame path (pft_lf.cu)
+  int lf_chunk = 0;         // frames per pass of the large-frame path
+  void* d_ws = nullptr;     // its workspace
 };
 
 namespace pfth {
@@ -40,5 +43,10 @@ int tc_build_tables(pft_plan* plan);
 int tc_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void* stream);
 int tc_build_adjoint_table(pft_plan* plan, const double* d_a);
 int tc_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void* stream);
+
+// Large frames, n in {2048, 4096, 8192} with M = 128 (pft_lf.cu).
+bool lf_supported(int n, int M, int p);
+int lf_build(pft_plan* plan);
+int lf_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void* stream);
 
 }  // namespace pfth
