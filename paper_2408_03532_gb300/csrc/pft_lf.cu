@@ -1,4 +1,4 @@
-// Large-frame PFT (the paper's regime n >> M): n = 2048, 4096 or 8192 with
+// Large-frame PFT (the paper's regime n >> M): n = 2048 ... 16384 with
 // M = 128, p = 64 (m~/p = 1, so r = 13 at eps = 1e-7) and q = n / 64, in
 // split-BF16 tensor-core arithmetic for stage A and FP32 for stage B.
 //
@@ -46,7 +46,7 @@ constexpr uint32_t X_LBO = 16 * CM + 32;          // padded: conflict-free 4-byt
 constexpr uint32_t X_COMP = (kC / 8) * X_LBO;
 constexpr uint32_t X_STAGE = 4 * X_COMP;
 constexpr uint32_t B_LBO = (kJ / 8) * CM;         // 256: table core matrices along K
-constexpr uint32_t TAB_MAX = 2 * (128 / 8) * B_LBO;  // hi + lo at q = 128: 8 KB
+constexpr uint32_t TAB_MAX = 2 * (256 / 8) * B_LBO;  // hi + lo at q = 256: 16 KB
 constexpr uint32_t OFF_TAB = 0;
 constexpr uint32_t OFF_X = TAB_MAX;
 constexpr uint32_t OFF_BAR = OFF_X + kStages * X_STAGE;
@@ -70,6 +70,14 @@ __device__ __forceinline__ void split_store2(uint8_t* base, uint32_t comp_bytes,
   const __nv_bfloat162 lo = __floats2bfloat162_rn(a - hf.x, b - hf.y);
   *reinterpret_cast<__nv_bfloat162*>(base + off) = hi;
   *reinterpret_cast<__nv_bfloat162*>(base + comp_bytes + off) = lo;
+}
+
+__device__ __forceinline__ float4 ld_stream(const float2* p, uint64_t pol) {
+  float4 r;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(p), "l"(pol));
+  return r;
 }
 
 // Stage A of `nrows` rows of length 64 Q (row stride = row length); the tile
@@ -192,6 +200,10 @@ __global__ void __launch_bounds__(kThreadsA, 1)
     const int half = lane >> 4, e = lane & 15;
     const uint32_t kk = (uint32_t)(e >> 2), wd = (uint32_t)(e & 3);
     const long long total = ntiles * kChunks;
+    // the frames are read once: mark them first to leave L2, so that the
+    // stage-A output C stays there for stage B
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     using Buf = float4[kRowsPerThread];
     auto load = [&](long long L, Buf& r) {
       if (L >= total) return;
@@ -202,7 +214,7 @@ __global__ void __launch_bounds__(kThreadsA, 1)
         const int m = cw * (2 * kRowsPerThread) + 2 * j + half;
         const long long row = 2 * tile + (m >> 6);
         const float2* src = x + row * (long long)N + (m & 63) * Q + c * kC + 2 * e;
-        r[j] = __ldg(reinterpret_cast<const float4*>(src));
+        r[j] = ld_stream(src, pol);
       }
     };
     auto step = [&](long long L, Buf& r) -> bool {
@@ -253,16 +265,22 @@ using F64 = Fft<kP>;
 __global__ void __launch_bounds__(kThreadsB)
     k_lf_stage_b(const float2* __restrict__ C, long long nrows, int rows_per_frame, float2* __restrict__ out,
                  const float2* __restrict__ gW, const float2* __restrict__ gtw) {
+  // Lane l ends the 64-point FFT holding rho = 2 bitrev(l) + pos; its outputs
+  // are t_idx = rho + 64 hi. W' and the staging buffer are stored in "slot"
+  // order s = (2 pos + hi) 32 + l, so that a warp touches 32 consecutive
+  // entries (no bank conflicts).
   __shared__ float2 tw[F64::TAB];
   __shared__ float2 sW[kRt * kMl];
-  __shared__ float2 stage[kMl][kRowsB];
+  __shared__ float2 stage[kRowsB][kMl];
   F64::fill(tw, gtw);
-  for (int i = threadIdx.x; i < kRt * kMl; i += blockDim.x) sW[i] = gW[i];
+  for (int i = threadIdx.x; i < kRt * kMl; i += blockDim.x) {
+    const int j = i / kMl, sl = i % kMl, l = sl % 32, pos = (sl / 32) >> 1, hi = (sl / 32) & 1;
+    sW[i] = gW[j * kMl + 2 * bitrev<32>(l) + pos + kP * hi];
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   typename F64::Net net;
   F64::init_net(net, lane, tw);
-  const int rho0 = 2 * bitrev<32>(lane);
   for (long long r0 = (long long)blockIdx.x * kRowsB; r0 < nrows; r0 += (long long)gridDim.x * kRowsB) {
     const long long row = r0 + warp;
     float2 ch[kRt][2];
@@ -276,18 +294,17 @@ __global__ void __launch_bounds__(kThreadsB)
     }
 #pragma unroll
     for (int pos = 0; pos < 2; ++pos) {
-      const int rho = rho0 + pos;
 #pragma unroll
       for (int hi = 0; hi < 2; ++hi) {
-        const int ti = rho + hi * kP;  // t = ti - 64, t mod 64 = rho
+        const int sl = (2 * pos + hi) * 32 + lane;  // t_idx = 2 bitrev(lane) + pos + 64 hi
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < kRt; ++j) {
-          const float2 w = sW[j * kMl + ti];
+          const float2 w = sW[j * kMl + sl];
           acc.x = fmaf(w.x, ch[j][pos].x, fmaf(-w.y, ch[j][pos].y, acc.x));
           acc.y = fmaf(w.x, ch[j][pos].y, fmaf(w.y, ch[j][pos].x, acc.y));
         }
-        stage[ti][warp] = acc;
+        stage[warp][sl] = acc;
       }
     }
     __syncthreads();
@@ -296,7 +313,9 @@ __global__ void __launch_bounds__(kThreadsB)
     float2* o = out + f * (long long)kMl * rows_per_frame + rin;
     for (int i = threadIdx.x; i < kMl * kRowsB / 2; i += blockDim.x) {
       const int ti = i / (kRowsB / 2), part = i % (kRowsB / 2);
-      const float2 a = stage[ti][2 * part], b = stage[ti][2 * part + 1];
+      const int r = ti & (kP - 1);
+      const int sl = ((r & 1) * 2 + (ti >> 6)) * 32 + bitrev<32>(r >> 1);
+      const float2 a = stage[2 * part][sl], b = stage[2 * part + 1][sl];
       *reinterpret_cast<float4*>(o + (long long)ti * rows_per_frame + 2 * part) = make_float4(a.x, a.y, b.x, b.y);
     }
     __syncthreads();
@@ -338,6 +357,7 @@ int stage_a(int q, const float2* x, long long nrows, float2* C, const void* tab,
     case 32: return launch_stage_a<32>(x, nrows, C, tab, status, st);
     case 64: return launch_stage_a<64>(x, nrows, C, tab, status, st);
     case 128: return launch_stage_a<128>(x, nrows, C, tab, status, st);
+    case 256: return launch_stage_a<256>(x, nrows, C, tab, status, st);
     default: return pfth::set_error(PFT_ERR_UNSUPPORTED, "large-frame block length q=%d not built", q);
   }
 }
@@ -352,12 +372,301 @@ int stage_b(const float2* C, long long nrows, int rows_per_frame, float2* out, c
   return PFT_OK;
 }
 
+
+// ============================================================== adjoint
+// Per axis the adjoint of Algorithm 2 reverses each step:
+//   H[rho][j] = sum_{t = rho mod 64} conj(W'[t][j]) y[t]
+//   E[k][j]   = sum_rho e^{+2 pi i rho k / 64} H[rho][j]        (F^H)
+//   x[q k + l] = sum_j B[l][j] E[k][j]                         (B real)
+// k_lf_stage_b_adj reads its rows transposed (the layout k_lf_stage_b
+// writes) and produces E[row][j][k]; k_lf_expand expands every block on
+// tensor cores (M = 128 blocks, N = q values l, K = 16 terms j).
+
+__global__ void __launch_bounds__(kThreadsB)
+    k_lf_stage_b_adj(const float2* __restrict__ in, long long nrows, int rows_per_frame, float2* __restrict__ E,
+                     const float2* __restrict__ gW, const float2* __restrict__ gtw) {
+  __shared__ float2 tw[F64::TAB];
+  __shared__ float2 sW[kRt * kMl];
+  __shared__ float2 stage[kRowsB][kMl];
+  F64::fill(tw, gtw);
+  for (int i = threadIdx.x; i < kRt * kMl; i += blockDim.x) {
+    const int j = i / kMl, sl = i % kMl, l = sl % 32, pos = (sl / 32) >> 1, hi = (sl / 32) & 1;
+    sW[i] = gW[j * kMl + 2 * bitrev<32>(l) + pos + kP * hi];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  typename F64::Net net;
+  F64::init_net(net, lane, tw);
+  for (long long r0 = (long long)blockIdx.x * kRowsB; r0 < nrows; r0 += (long long)gridDim.x * kRowsB) {
+    const long long f = r0 / rows_per_frame;
+    const int rin = (int)(r0 % rows_per_frame);
+    const float2* ip = in + f * (long long)kMl * rows_per_frame + rin;
+    for (int i = threadIdx.x; i < kMl * kRowsB / 2; i += blockDim.x) {
+      const int ti = i / (kRowsB / 2), part = i % (kRowsB / 2);
+      const int r = ti & (kP - 1);
+      const int sl = ((r & 1) * 2 + (ti >> 6)) * 32 + bitrev<32>(r >> 1);
+      const float4 v = __ldg(reinterpret_cast<const float4*>(ip + (long long)ti * rows_per_frame + 2 * part));
+      stage[2 * part][sl] = make_float2(v.x, v.y);
+      stage[2 * part + 1][sl] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+    const long long row = r0 + warp;
+    float2* dst = E + row * (long long)(kRt * kP);
+#pragma unroll
+    for (int j = 0; j < kRt; ++j) {
+      float2 v[2];
+#pragma unroll
+      for (int pos = 0; pos < 2; ++pos) {
+        float2 h = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int hi = 0; hi < 2; ++hi) {
+          const int sl = (2 * pos + hi) * 32 + lane;
+          const float2 w = sW[j * kMl + sl], yv = stage[warp][sl];
+          h.x = fmaf(w.x, yv.x, fmaf(w.y, yv.y, h.x));   // conj(w) * y
+          h.y = fmaf(w.x, yv.y, fmaf(-w.y, yv.x, h.y));
+        }
+        v[pos] = h;
+      }
+      F64::adj(v, lane, tw, net);  // v[e] = E[lane + 32 e][j]
+      dst[j * kP + lane] = v[0];
+      dst[j * kP + lane + 32] = v[1];
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int kStagesE = 4;
+constexpr uint32_t E_LBO = 16 * CM;               // K-direction step (j 0..7 -> 8..15)
+constexpr uint32_t E_COMP = 2 * E_LBO;            // [128 blocks][16 j] BF16
+constexpr uint32_t E_STAGE = 4 * E_COMP;          // re hi, re lo, im hi, im lo
+constexpr int kStgStride = 17;                    // staging row stride (complex), odd
+constexpr uint32_t OFF2_TAB = 0;                  // B^T hi | lo, up to 16 KB
+constexpr uint32_t OFF2_E = 16384;
+constexpr uint32_t OFF2_STG = OFF2_E + kStagesE * E_STAGE;
+constexpr uint32_t STG_BYTES = 4 * 32 * kStgStride * 8;
+constexpr uint32_t OFF2_BAR = OFF2_STG + STG_BYTES;
+constexpr int NBAR2 = 2 * kStagesE + 2 * 4 + 1;
+constexpr uint32_t OFF2_SLOT = OFF2_BAR + 8 * NBAR2;
+constexpr uint32_t OFF2_ABORT = OFF2_SLOT + 8;
+constexpr uint32_t SMEM_E = OFF2_ABORT + 8;
+static_assert(SMEM_E <= 232448, "shared memory layout too large");
+constexpr int kLdWarpsE = 4, kLdWarp0E = 8;
+constexpr int kThreadsE = 32 * (kLdWarp0E + kLdWarpsE);  // warps 5-7 idle
+
+// x[row][q k + l] = sum_j B[l][j] E[row][j][k]; tile t = rows 2t, 2t + 1.
+template <int Q>
+__global__ void __launch_bounds__(kThreadsE, 1)
+    k_lf_expand(const float2* __restrict__ E, long long nrows, float2* __restrict__ x,
+                const uint4* __restrict__ tab, int* status) {
+  constexpr int N = kP * Q;
+  constexpr uint32_t T_LBO = (Q / 8) * CM;         // B^T: [j / 8][l / 8][8][16 B]
+  constexpr uint32_t T_HALF = 2 * T_LBO;
+  constexpr uint32_t ACC = 2 * Q;                  // D_re | D_im
+  constexpr int kBufs = (512 / ACC) < 4 ? (512 / ACC) : 4;
+  constexpr uint32_t TCOLS = kBufs * ACC <= 32 ? 32 : (kBufs * ACC <= 64 ? 64 : (kBufs * ACC <= 128 ? 128 :
+                             (kBufs * ACC <= 256 ? 256 : 512)));
+  static_assert(2 * T_HALF <= OFF2_E && Q % 16 == 0 && Q <= 256, "block length");
+  extern __shared__ __align__(128) uint8_t sm[];
+  const uint32_t sb = smem_u32(sm);
+  const uint32_t bar = sb + OFF2_BAR;
+  const uint32_t E_FULL = bar, E_EMPTY = bar + 8 * kStagesE, ACC_FULL = bar + 16 * kStagesE,
+                 ACC_EMPTY = ACC_FULL + 32, DONE = ACC_FULL + 64;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF2_ABORT);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + OFF2_SLOT);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (int i = threadIdx.x; i < (int)(2 * T_HALF / 16); i += blockDim.x)
+    reinterpret_cast<uint4*>(sm + OFF2_TAB)[i] = __ldg(tab + i);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStagesE; ++s) {
+      mbar_init(E_FULL + 8 * s, kLdWarpsE);
+      mbar_init(E_EMPTY + 8 * s, 1);
+    }
+    for (int b = 0; b < 4; ++b) {
+      mbar_init(ACC_FULL + 8 * b, 1);
+      mbar_init(ACC_EMPTY + 8 * b, kEpiWarps);
+    }
+    mbar_init(DONE, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == kMmaWarp) {
+    tmem_alloc(smem_u32(tslot), TCOLS);
+    tmem_relinquish();
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const long long ntile_all = nrows / 2;
+  const long long ntiles = blockIdx.x < ntile_all ? (ntile_all - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (warp == kMmaWarp) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(128, Q);
+      const uint64_t th = sdesc(sb + OFF2_TAB, T_LBO, CM), tl = sdesc(sb + OFF2_TAB + T_HALF, T_LBO, CM);
+      for (long long T = 0; T < ntiles; ++T) {
+        const int b = (int)(T % kBufs);
+        const uint32_t v = (uint32_t)(T / kBufs);
+        const int s = (int)(T % kStagesE);
+        const uint32_t u = (uint32_t)(T / kStagesE);
+        if (!mbar_wait(ACC_EMPTY + 8 * b, (v & 1u) ^ 1u, abort_flag, kWaitNs)) break;
+        if (!mbar_wait(E_FULL + 8 * s, u & 1u, abort_flag, kWaitNs)) break;
+        tc_fence_after();
+        const uint32_t es = sb + OFF2_E + s * E_STAGE;
+        const uint64_t rh = sdesc(es, E_LBO, CM), rl = sdesc(es + E_COMP, E_LBO, CM);
+        const uint64_t ih = sdesc(es + 2 * E_COMP, E_LBO, CM), il = sdesc(es + 3 * E_COMP, E_LBO, CM);
+        const uint32_t dr = tmem + b * ACC, di = dr + Q;
+        mma_bf16(dr, rh, th, idesc, 0);
+        mma_bf16(dr, rl, th, idesc, 1);
+        mma_bf16(dr, rh, tl, idesc, 1);
+        mma_bf16(di, ih, th, idesc, 0);
+        mma_bf16(di, il, th, idesc, 1);
+        mma_bf16(di, ih, tl, idesc, 1);
+        mma_commit(E_EMPTY + 8 * s);
+        mma_commit(ACC_FULL + 8 * b);
+      }
+      volatile int never = 0;
+      mma_commit(DONE);
+      mbar_wait(DONE, 0, &never, kWaitNs);
+    }
+    __syncwarp();
+  } else if (warp < kEpiWarps) {
+    // TMEM lane 32 q + lane = block k = 32 (q & 1) + lane of row 2t + (q >> 1)
+    const int q = warp;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    float2* stg = reinterpret_cast<float2*>(sm + OFF2_STG) + q * 32 * kStgStride;
+    for (long long T = 0; T < ntiles; ++T) {
+      const long long tile = blockIdx.x + T * gridDim.x;
+      const int b = (int)(T % kBufs);
+      const uint32_t v = (uint32_t)(T / kBufs);
+      if (!mbar_wait(ACC_FULL + 8 * b, v & 1u, abort_flag, kWaitNs)) break;
+      tc_fence_after();
+      const long long row = 2 * tile + (q >> 1);
+      float2* xr = x + row * (long long)N + (q & 1) * 32 * Q;
+      for (int c = 0; c < Q / 16; ++c) {
+        float re[16], im[16];
+        tmem_ld16(tmem + lane_off + b * ACC + 16 * c, re);
+        tmem_ld16(tmem + lane_off + b * ACC + Q + 16 * c, im);
+        tmem_wait_ld();
+        if (c == Q / 16 - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(ACC_EMPTY + 8 * b);
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) stg[lane * kStgStride + e] = make_float2(re[e], im[e]);
+        __syncwarp();
+        // 32 blocks x 16 values: 8 lanes per block, 16 bytes each, 4 blocks per step
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int blk = it * 4 + (lane >> 3), part = lane & 7;
+          const float2 a = stg[blk * kStgStride + 2 * part], b2 = stg[blk * kStgStride + 2 * part + 1];
+          *reinterpret_cast<float4*>(xr + blk * Q + 16 * c + 2 * part) = make_float4(a.x, a.y, b2.x, b2.y);
+        }
+        __syncwarp();
+      }
+    }
+  } else if (warp >= kLdWarp0E) {
+    // item i: j pair jp = word + 4 (i & 1), block m = (4 w + (i >> 1)) 8 + mb
+    const int w = warp - kLdWarp0E, word = lane >> 3, mb = lane & 7;
+    for (long long T = 0; T < ntiles; ++T) {
+      const long long tile = blockIdx.x + T * gridDim.x;
+      const int s = (int)(T % kStagesE);
+      const uint32_t u = (uint32_t)(T / kStagesE);
+      float2 va[8], vb[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int jp = word + 4 * (i & 1), m = (4 * w + (i >> 1)) * 8 + mb;
+        const float2* src = E + (2 * tile + (m >> 6)) * (long long)(kRt * kP) + (m & 63);
+        va[i] = 2 * jp < kRt ? __ldg(src + 2 * jp * kP) : make_float2(0.f, 0.f);
+        vb[i] = 2 * jp + 1 < kRt ? __ldg(src + (2 * jp + 1) * kP) : make_float2(0.f, 0.f);
+      }
+      if (!mbar_wait(E_EMPTY + 8 * s, (u & 1u) ^ 1u, abort_flag, kWaitNs)) break;
+      uint8_t* es = sm + OFF2_E + s * E_STAGE;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int jp = word + 4 * (i & 1), m = (4 * w + (i >> 1)) * 8 + mb;
+        const uint32_t off = (uint32_t)(jp >> 2) * E_LBO + (uint32_t)m * 16 + (uint32_t)(jp & 3) * 4;
+        split_store2(es, E_COMP, off, va[i].x, vb[i].x);
+        split_store2(es + 2 * E_COMP, E_COMP, off, va[i].y, vb[i].y);
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(E_FULL + 8 * s);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TCOLS);
+  }
+  if (threadIdx.x == 0 && *abort_flag) {
+    *reinterpret_cast<volatile int*>(status) = PFT_ERR_TIMEOUT;
+    __threadfence_system();
+  }
+}
+
+// B^T for the expansion: [N = l][K = j] K-major, hi | lo, each
+// [j / 8][l / 8][8][16 B].
+__global__ void k_lf_table_adj(int q, int r, const double* __restrict__ a, uint16_t* __restrict__ tab) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= q * kJ) return;
+  const int l = id / kJ, j = id % kJ;
+  const double v = j < r ? a[j] * ((j == 0) ? 1.0 : pow((double)(q - 2 * l) / (double)q, (double)j)) : 0.0;
+  uint16_t hi, lo;
+  split_bf16(v, hi, lo);
+  const uint32_t t_lbo = (uint32_t)(q / 8) * CM;
+  const uint32_t at = ((uint32_t)(j / 8) * t_lbo + (uint32_t)(l / 8) * CM + (uint32_t)(l % 8) * 16 +
+                       (uint32_t)(j % 8) * 2) / 2;
+  tab[at] = hi;
+  tab[at + t_lbo] = lo;  // lo half starts 2 t_lbo bytes = t_lbo entries later
+}
+
+template <int Q>
+int launch_expand(const float2* E, long long nrows, float2* x, const void* tab, int* status, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    PFT_CUDA_TRY(cudaFuncSetAttribute(k_lf_expand<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_E));
+    attr = true;
+  }
+  long long grid = pfth::sm_count();
+  if (grid > nrows / 2) grid = nrows / 2;
+  if (grid < 1) return PFT_OK;
+  k_lf_expand<Q><<<(unsigned)grid, kThreadsE, SMEM_E, st>>>(E, nrows, x, (const uint4*)tab, status);
+  PFT_CUDA_TRY(cudaGetLastError());
+  return PFT_OK;
+}
+
+int expand(int q, const float2* E, long long nrows, float2* x, const void* tab, int* status, cudaStream_t st) {
+  switch (q) {
+    case 32: return launch_expand<32>(E, nrows, x, tab, status, st);
+    case 64: return launch_expand<64>(E, nrows, x, tab, status, st);
+    case 128: return launch_expand<128>(E, nrows, x, tab, status, st);
+    case 256: return launch_expand<256>(E, nrows, x, tab, status, st);
+    default: return pfth::set_error(PFT_ERR_UNSUPPORTED, "large-frame block length q=%d not built", q);
+  }
+}
+
+int stage_b_adj(const float2* in, long long nrows, int rows_per_frame, float2* E, const float2* W, cudaStream_t st) {
+  const float2* tw = pfth::twiddles(kP);
+  if (!tw) return PFT_ERR_CUDA;
+  long long groups = nrows / kRowsB;
+  long long grid = groups < 8LL * pfth::sm_count() ? groups : 8LL * pfth::sm_count();
+  k_lf_stage_b_adj<<<(unsigned)grid, kThreadsB, 0, st>>>(in, nrows, rows_per_frame, E, W, tw);
+  PFT_CUDA_TRY(cudaGetLastError());
+  return PFT_OK;
+}
+
 }  // namespace
 
 namespace pfth {
 
 bool lf_supported(int n, int M, int p) {
-  return M == kMl && (p == 0 || p == kP) && (n == 2048 || n == 4096 || n == 8192);
+  return M == kMl && (p == 0 || p == kP) && (n == 2048 || n == 4096 || n == 8192 || n == 16384);
 }
 
 int lf_build(pft_plan* plan) {
@@ -371,6 +680,9 @@ int lf_build(pft_plan* plan) {
   PFT_CUDA_TRY(cudaMemcpy(d_a, a, sizeof(double) * plan->r1, cudaMemcpyHostToDevice));
   PFT_CUDA_TRY(cudaMalloc(&plan->d_tc, 2 * (q / 8) * B_LBO));
   k_lf_table<<<(q * kJ + 127) / 128, 128>>>(q, plan->r1, d_a, reinterpret_cast<uint16_t*>(plan->d_tc));
+  PFT_CUDA_TRY(cudaGetLastError());
+  PFT_CUDA_TRY(cudaMalloc(&plan->d_tc_adj, 4 * (q / 8) * CM));
+  k_lf_table_adj<<<(q * kJ + 127) / 128, 128>>>(q, plan->r1, d_a, reinterpret_cast<uint16_t*>(plan->d_tc_adj));
   PFT_CUDA_TRY(cudaGetLastError());
   PFT_CUDA_TRY(cudaDeviceSynchronize());
   PFT_CUDA_TRY(cudaFree(d_a));
@@ -407,6 +719,32 @@ int lf_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void
     if (rc == PFT_OK) rc = stage_b(Cw, nf * n, n, TT, W, st);
     if (rc == PFT_OK) rc = stage_a(plan->q1, TT, nf * kMl, C2, plan->d_tc, plan->d_status, st);
     if (rc == PFT_OK) rc = stage_b(C2, nf * kMl, kMl, yf, W, st);
+    if (rc != PFT_OK) return rc;
+  }
+  return PFT_OK;
+}
+
+int lf_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void* stream) {
+  if (*plan->h_status != PFT_OK) {
+    const int st = *plan->h_status;
+    *plan->h_status = PFT_OK;
+    return set_error(st, "a device-side wait of an earlier large-frame launch timed out");
+  }
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int n = plan->n1;
+  const long long f = plan->lf_chunk;
+  float2* Ew = (float2*)plan->d_ws;
+  float2* TT = Ew + f * (long long)n * kRt * kP;
+  float2* E2 = TT + f * (long long)kMl * n;
+  const float2* W = plan->d_W;
+  for (long long f0 = 0; f0 < batch; f0 += f) {
+    const long long nf = std::min<long long>(f, batch - f0);
+    const float2* yf = (const float2*)y + f0 * (long long)kMl * kMl;
+    float2* xf = (float2*)x + f0 * (long long)n * n;
+    int rc = stage_b_adj(yf, nf * kMl, kMl, E2, W, st);
+    if (rc == PFT_OK) rc = expand(plan->q1, E2, nf * kMl, TT, plan->d_tc_adj, plan->d_status, st);
+    if (rc == PFT_OK) rc = stage_b_adj(TT, nf * n, n, Ew, W, st);
+    if (rc == PFT_OK) rc = expand(plan->q1, Ew, nf * n, xf, plan->d_tc_adj, plan->d_status, st);
     if (rc != PFT_OK) return rc;
   }
   return PFT_OK;

@@ -440,7 +440,7 @@ int pft_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, voi
     if (batch == 0) return PFT_OK;
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
       return pfth::set_error(PFT_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
-    if (plan->lf) return pfth::set_error(PFT_ERR_UNSUPPORTED, "the large-frame adjoint is not built");
+    if (plan->lf) return pfth::lf_adjoint(plan, y, x, batch, stream);
     return pfth::tc_adjoint(plan, y, x, batch, stream);
   }
   return launch_frames(plan, y, x, batch, stream, true);

@@ -48,5 +48,6 @@ int tc_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void
 bool lf_supported(int n, int M, int p);
 int lf_build(pft_plan* plan);
 int lf_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void* stream);
+int lf_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void* stream);
 
 }  // namespace pfth
