@@ -240,6 +240,9 @@ def main() -> None:
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the built-in cluster-size heuristic instead of timing each size (for profilers, "
                          "whose per-launch overhead distorts the autotuner's timings)")
+    ap.add_argument("--no-pft-large", action="store_true")
+    ap.add_argument("--only-pft-large", action="store_true",
+                    help="run only the large-frame transforms and print their JSON (profiling target)")
     ap.add_argument("--only-pft-batch", action="store_true",
                     help="run only the standalone batched transform (--pft-frames frames) and print its JSON; "
                          "not a benchmark line (used as a small profiling target)")
@@ -263,6 +266,10 @@ def main() -> None:
     libbuild.build()
     pft.load()
 
+    if args.only_pft_large:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps(measure_pft_large(pft, torch, dev, torch.cuda.current_stream(dev), flush)))
+        return
     if args.only_pft_batch:
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         print(json.dumps(measure_pft_batch(pft, torch, dev, torch.cuda.current_stream(dev), flush, args.pft_frames)))
@@ -354,6 +361,7 @@ def main() -> None:
 
     pft_batch = None if args.no_pft_batch else measure_pft_batch(pft, torch, dev, stream, flush, args.pft_frames)
     batch64 = None if args.no_batch64 else measure_batch64(pft, synth, torch, dev, stream, flush)
+    pft_large = None if args.no_pft_large else measure_pft_large(pft, torch, dev, stream, flush)
 
     # roofline of the dominant kernel (per sweep of launches of that kernel)
     pinfo = pft.Plan(n, M).info
@@ -385,7 +393,7 @@ def main() -> None:
                         "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                 "gpu_launches": 2 * launches_per_sweep * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "time_to_target": ttt, "pft_batch": pft_batch, "batch64": batch64, "wall_s": wall, "colours": ncol,
+                "time_to_target": ttt, "pft_batch": pft_batch, "pft_large": pft_large, "batch64": batch64, "wall_s": wall, "colours": ncol,
                 "autotune": tuning}
         print(json.dumps(line))
     if world > 1:
@@ -504,6 +512,56 @@ def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32
             "speedup_vs_fft_crop": fft_crop_ms / f_ms,
             "max_rel_diff_vs_fp32": {"forward": rel_f, "adjoint": rel_a},
             "roofline": {"forward": roof("k_pft_tc_fwd", f_ms), "adjoint": roof("k_pft_tc_adj", a_ms)}}
+
+
+def measure_pft_large(pft, torch, dev, stream, flush, cases=((8192, 4), (16384, 1)), reps: int = 5) -> dict:
+    """The large-frame regime (M = 128, p = 64, r = 13): split-BF16 forward and
+    adjoint on frames with i.i.d. N(0, 1) parts, each timed with CUDA events
+    (inputs of 2 GiB, larger than L2, L2 flushed before every call), against
+    cuFFT's full 2-D FFT followed by the crop (a GPU library baseline, timed the
+    same way). Algorithmic bytes per frame: 8 n^2 + 8 M^2."""
+    peak, kind = hbm_peak()
+    M = 128
+    out = {"M": M, "hbm_peak_gbs": peak, "peak_kind": kind}
+
+    def timed(fn):
+        fn()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    for n, frames in cases:
+        x = torch.randn(frames, n, n, dtype=torch.complex64, device=dev, generator=torch.Generator(dev).manual_seed(n))
+        plan = pft.Plan(n, M, precision=pft.PREC_SPLIT_BF16)
+        y = torch.empty(frames, M, M, dtype=torch.complex64, device=dev)
+        xa = torch.empty_like(x)
+        idx = torch.cat([torch.arange(n - M // 2, n), torch.arange(0, M // 2)]).to(dev)
+
+        def fft_crop():
+            return torch.fft.fft2(x)[:, idx][:, :, idx]
+
+        f_ms = timed(lambda: plan.forward(x, out=y))
+        a_ms = timed(lambda: plan.adjoint(y, out=xa))
+        c_ms = timed(fft_crop)
+        ref = fft_crop()
+        rel = float((torch.linalg.vector_norm((y - ref).reshape(frames, -1), dim=1)
+                     / torch.linalg.vector_norm(ref.reshape(frames, -1), dim=1)).max())
+        byts = frames * (8 * n * n + 8 * M * M)
+        out[f"n{n}"] = {"frames": frames, "p": plan.info["p1"], "q": plan.info["q1"], "r": plan.info["r1"],
+                        "forward_ms": f_ms, "forward_gbs": byts / f_ms / 1e6, "forward_frac": byts / f_ms / 1e6 / peak,
+                        "adjoint_ms": a_ms, "adjoint_gbs": byts / a_ms / 1e6, "adjoint_frac": byts / a_ms / 1e6 / peak,
+                        "cufft_crop_ms": c_ms, "speedup_vs_cufft_crop": c_ms / f_ms,
+                        "max_rel_diff_vs_exact_partial_dft": rel}
+        del x, y, xa, ref, plan
+        torch.cuda.empty_cache()
+    return out
 
 
 def measure_batch64(pft, synth, torch, dev, stream, flush, reps: int = 3) -> dict:
