@@ -11,13 +11,12 @@
 // tcgen05 (M = 128 blocks (row, k) of q contiguous values, K = l, N = 16 for
 // the 13 terms), with every operand split into BF16 hi + lo and three partial
 // products per term. Stage B (13 FFTs of size 64 per row and the W' combine)
-// runs on CUDA cores in FP32 and writes the row's M outputs transposed, so
-// the second axis is the same two kernels applied to the rows of the
-// transposed intermediate T^T[t2][u]:
-//   k_lf_stage_a(x rows)   -> C    [rows][13][64]
-//   k_lf_stage_b(C)        -> T^T  [frame][128][n]
-//   k_lf_stage_a(T^T rows) -> C'   [rows][13][64]
-//   k_lf_stage_b(C')       -> Y    [frame][128][128]
+// runs in FP32 on CUDA cores in the same kernel's epilogue, straight from the
+// tensor-memory accumulators, and writes the row's M outputs transposed, so
+// the second axis is the same kernel applied to the rows of the transposed
+// intermediate T^T[t2][u]:
+//   k_lf_stage_a(x rows)   -> T^T  [frame][128][n]
+//   k_lf_stage_a(T^T rows) -> Y    [frame][128][128]
 // Every wait is bounded (2 s); a timeout sets the plan's status word.
 #include <cuda_bf16.h>
 
@@ -39,7 +38,7 @@ constexpr int kMl = 128;               // output side M
 constexpr int kRt = 13;                // polynomial terms r
 constexpr int kJ = 16;                 // r padded to the MMA N
 constexpr int kC = 32;                 // K values (l) per operand stage
-constexpr int kStages = 6;
+constexpr int kStages = 5;
 constexpr int kAccBufs = 4;
 constexpr uint32_t CM = 128;
 constexpr uint32_t X_LBO = 16 * CM + 32;          // padded: conflict-free 4-byte stores
@@ -49,7 +48,13 @@ constexpr uint32_t B_LBO = (kJ / 8) * CM;         // 256: table core matrices al
 constexpr uint32_t TAB_MAX = 2 * (256 / 8) * B_LBO;  // hi + lo at q = 256: 16 KB
 constexpr uint32_t OFF_TAB = 0;
 constexpr uint32_t OFF_X = TAB_MAX;
-constexpr uint32_t OFF_BAR = OFF_X + kStages * X_STAGE;
+// stage B in the epilogue: Fft<64> tables, W' in slot order, the half-row
+// exchange of C between the two warps of a row, and their partial sums
+constexpr uint32_t OFF_TW = OFF_X + kStages * X_STAGE;
+constexpr uint32_t OFF_W = OFF_TW + 160 * 8;
+constexpr uint32_t OFF_XCH = OFF_W + kRt * kMl * 8;
+constexpr uint32_t OFF_PS = OFF_XCH + 2 * kRt * 32 * 8;
+constexpr uint32_t OFF_BAR = OFF_PS + 2 * kMl * 8;
 constexpr int NBAR = 2 * kStages + 2 * kAccBufs + 1;
 constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * NBAR;
 constexpr uint32_t OFF_ABORT = OFF_SLOT + 8;
@@ -72,6 +77,37 @@ __device__ __forceinline__ void split_store2(uint8_t* base, uint32_t comp_bytes,
   *reinterpret_cast<__nv_bfloat162*>(base + comp_bytes + off) = lo;
 }
 
+using F64 = Fft<kP>;
+constexpr int kThreadsB = 256;              // stage-B adjoint: one warp per row
+constexpr int kRowsB = kThreadsB / 32;
+
+// W'[j][t_idx] (t_idx < 128) in "slot" order s = (2 pos + hi) 32 + l, where
+// lane l ends the 64-point FFT holding rho = 2 bitrev(l) + pos and owns the
+// outputs t_idx = rho + 64 hi: a warp then reads 32 consecutive entries.
+__device__ __forceinline__ void fill_w_slots(float2* sW, const float2* __restrict__ gW) {
+  for (int i = threadIdx.x; i < kRt * kMl; i += blockDim.x) {
+    const int j = i / kMl, sl = i % kMl, l = sl % 32, pos = (sl / 32) >> 1, hi = (sl / 32) & 1;
+    sW[i] = gW[j * kMl + 2 * bitrev<32>(l) + pos + kP * hi];
+  }
+}
+
+__device__ __forceinline__ void pair_barrier(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// Both warps of a pair get the AND of their flags (so that they leave the
+// tile loop together and never wait at a pair barrier the other skips).
+__device__ __forceinline__ bool pair_all(bool v, int id) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, 64, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id)
+      : "memory");
+  return r != 0;
+}
+
 __device__ __forceinline__ float4 ld_stream(const float2* p, uint64_t pol) {
   float4 r;
   asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
@@ -80,12 +116,16 @@ __device__ __forceinline__ float4 ld_stream(const float2* p, uint64_t pol) {
   return r;
 }
 
-// Stage A of `nrows` rows of length 64 Q (row stride = row length); the tile
-// t covers rows 2t, 2t + 1, i.e. 128 blocks (row, k) of Q values.
+// Stages A and B of `nrows` rows of length 64 Q (row stride = row length);
+// the tile t covers rows 2t, 2t + 1, i.e. 128 blocks (row, k) of Q values.
+// Stage A runs on tensor cores; the four epilogue warps (two per row) then
+// run stage B on the accumulators and write the row's 128 outputs to
+// out[frame][t_idx][row in frame] (rows_per_frame rows per frame).
 template <int Q>
 __global__ void __launch_bounds__(kThreadsA, 1)
-    k_lf_stage_a(const float2* __restrict__ x, long long nrows, float2* __restrict__ C,
-                 const uint4* __restrict__ tab, int* status) {
+    k_lf_stage_a(const float2* __restrict__ x, long long nrows, int rows_per_frame, float2* __restrict__ out,
+                 const uint4* __restrict__ tab, const float2* __restrict__ gW, const float2* __restrict__ gtw,
+                 int* status) {
   constexpr int N = kP * Q;
   constexpr int kChunks = Q / kC;
   constexpr uint32_t TAB_BYTES = 2 * (Q / 8) * B_LBO;
@@ -102,6 +142,10 @@ __global__ void __launch_bounds__(kThreadsA, 1)
 
   for (int i = threadIdx.x; i < (int)(TAB_BYTES / 16); i += blockDim.x)
     reinterpret_cast<uint4*>(sm + OFF_TAB)[i] = __ldg(tab + i);
+  float2* s_tw = reinterpret_cast<float2*>(sm + OFF_TW);
+  float2* s_w = reinterpret_cast<float2*>(sm + OFF_W);
+  F64::fill(s_tw, gtw);
+  fill_w_slots(s_w, gW);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(X_FULL + 8 * s, kLdWarps);
@@ -174,14 +218,23 @@ __global__ void __launch_bounds__(kThreadsA, 1)
     }
     __syncwarp();
   } else if (warp < kEpiWarps) {
-    // TMEM lane m = 32 q + lane: block k = 32 (q & 1) + lane of row 2t + (q >> 1)
-    const int q = warp;
+    // TMEM lane m = 32 q + lane: block k = 32 h + lane of row r = q >> 1
+    // (h = q & 1). Warp h = 0 of a row runs the FFTs of j = 0..6, warp h = 1
+    // those of j = 7..12; each first hands the other the half of C it lacks.
+    const int q = warp, r = q >> 1, h = q & 1;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    constexpr int kJ0 = 7;
+    const int jlo = h ? kJ0 : 0, jhi = h ? kRt : kJ0;
+    float2* xch = reinterpret_cast<float2*>(sm + OFF_XCH) + r * kRt * 32;
+    float2* ps = reinterpret_cast<float2*>(sm + OFF_PS) + r * kMl;
+    typename F64::Net net;
+    F64::init_net(net, lane, s_tw);
     for (long long T = 0; T < ntiles; ++T) {
       const long long tile = blockIdx.x + T * gridDim.x;
       const int b = (int)(T % kAccBufs);
       const uint32_t v = (uint32_t)(T / kAccBufs);
-      if (!mbar_wait(ACC_FULL + 8 * b, v & 1u, abort_flag, kWaitNs)) break;
+      const bool got = mbar_wait(ACC_FULL + 8 * b, v & 1u, abort_flag, kWaitNs);
+      if (!pair_all(got, 1 + r)) break;
       tc_fence_after();
       float re[16], im[16];
       tmem_ld16(tmem + lane_off + b * ACC_COLS, re);
@@ -190,10 +243,44 @@ __global__ void __launch_bounds__(kThreadsA, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(ACC_EMPTY + 8 * b);
-      const long long row = 2 * tile + (q >> 1);
-      float2* dst = C + row * (long long)(kRt * kP) + (q & 1) * 32 + lane;
 #pragma unroll
-      for (int j = 0; j < kRt; ++j) dst[j * kP] = make_float2(re[j], im[j]);
+      for (int j = 0; j < kRt; ++j)
+        if (j < jlo || j >= jhi) xch[j * 32 + lane] = make_float2(re[j], im[j]);
+      pair_barrier(1 + r);
+      float2 acc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kRt; ++j) {
+        if (j < jlo || j >= jhi) continue;
+        const float2 mine = make_float2(re[j], im[j]), other = xch[j * 32 + lane];
+        float2 cv[2] = {h ? other : mine, h ? mine : other};  // k = lane, k = lane + 32
+        F64::fwd(cv, lane, s_tw, net);                          // cv[pos] = C^[2 bitrev(lane) + pos][j]
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float2 w = s_w[j * kMl + i * 32 + lane], c = cv[i >> 1];
+          acc[i].x = fmaf(w.x, c.x, fmaf(-w.y, c.y, acc[i].x));
+          acc[i].y = fmaf(w.x, c.y, fmaf(w.y, c.x, acc[i].y));
+        }
+      }
+      if (h) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ps[i * 32 + lane] = acc[i];
+      }
+      pair_barrier(1 + r);
+      if (!h) {
+        const long long row = 2 * tile + r;
+        const long long f = row / rows_per_frame;
+        const long long rin = row % rows_per_frame;
+        float2* o = out + f * (long long)kMl * rows_per_frame + rin;
+        const int rho0 = 2 * bitrev<32>(lane);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float2 p2 = ps[i * 32 + lane];
+          const int ti = rho0 + (i >> 1) + kP * (i & 1);   // slot i * 32 + lane
+          o[(long long)ti * rows_per_frame] = make_float2(acc[i].x + p2.x, acc[i].y + p2.y);
+        }
+      }
     }
   } else if (warp >= kLdWarp0) {
     const int cw = warp - kLdWarp0;
@@ -256,72 +343,6 @@ __global__ void __launch_bounds__(kThreadsA, 1)
   }
 }
 
-// Stage B of `nrows` rows (rows_per_frame rows per frame): one warp per row,
-// eight consecutive rows per CTA; writes out[frame][t_idx][row in frame].
-constexpr int kThreadsB = 256;
-constexpr int kRowsB = kThreadsB / 32;
-using F64 = Fft<kP>;
-
-__global__ void __launch_bounds__(kThreadsB)
-    k_lf_stage_b(const float2* __restrict__ C, long long nrows, int rows_per_frame, float2* __restrict__ out,
-                 const float2* __restrict__ gW, const float2* __restrict__ gtw) {
-  // Lane l ends the 64-point FFT holding rho = 2 bitrev(l) + pos; its outputs
-  // are t_idx = rho + 64 hi. W' and the staging buffer are stored in "slot"
-  // order s = (2 pos + hi) 32 + l, so that a warp touches 32 consecutive
-  // entries (no bank conflicts).
-  __shared__ float2 tw[F64::TAB];
-  __shared__ float2 sW[kRt * kMl];
-  __shared__ float2 stage[kRowsB][kMl];
-  F64::fill(tw, gtw);
-  for (int i = threadIdx.x; i < kRt * kMl; i += blockDim.x) {
-    const int j = i / kMl, sl = i % kMl, l = sl % 32, pos = (sl / 32) >> 1, hi = (sl / 32) & 1;
-    sW[i] = gW[j * kMl + 2 * bitrev<32>(l) + pos + kP * hi];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  typename F64::Net net;
-  F64::init_net(net, lane, tw);
-  for (long long r0 = (long long)blockIdx.x * kRowsB; r0 < nrows; r0 += (long long)gridDim.x * kRowsB) {
-    const long long row = r0 + warp;
-    float2 ch[kRt][2];
-    const float2* src = C + row * (long long)(kRt * kP);
-#pragma unroll
-    for (int j = 0; j < kRt; ++j) {
-      float2 v[2] = {__ldg(src + j * kP + lane), __ldg(src + j * kP + lane + 32)};
-      F64::fwd(v, lane, tw, net);  // v[pos] = C^[pos + 2 bitrev(lane)][j]
-      ch[j][0] = v[0];
-      ch[j][1] = v[1];
-    }
-#pragma unroll
-    for (int pos = 0; pos < 2; ++pos) {
-#pragma unroll
-      for (int hi = 0; hi < 2; ++hi) {
-        const int sl = (2 * pos + hi) * 32 + lane;  // t_idx = 2 bitrev(lane) + pos + 64 hi
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int j = 0; j < kRt; ++j) {
-          const float2 w = sW[j * kMl + sl];
-          acc.x = fmaf(w.x, ch[j][pos].x, fmaf(-w.y, ch[j][pos].y, acc.x));
-          acc.y = fmaf(w.x, ch[j][pos].y, fmaf(w.y, ch[j][pos].x, acc.y));
-        }
-        stage[warp][sl] = acc;
-      }
-    }
-    __syncthreads();
-    const long long f = r0 / rows_per_frame;
-    const int rin = (int)(r0 % rows_per_frame);
-    float2* o = out + f * (long long)kMl * rows_per_frame + rin;
-    for (int i = threadIdx.x; i < kMl * kRowsB / 2; i += blockDim.x) {
-      const int ti = i / (kRowsB / 2), part = i % (kRowsB / 2);
-      const int r = ti & (kP - 1);
-      const int sl = ((r & 1) * 2 + (ti >> 6)) * 32 + bitrev<32>(r >> 1);
-      const float2 a = stage[2 * part][sl], b = stage[2 * part + 1][sl];
-      *reinterpret_cast<float4*>(o + (long long)ti * rows_per_frame + 2 * part) = make_float4(a.x, a.y, b.x, b.y);
-    }
-    __syncthreads();
-  }
-}
-
 // Stage-A table B[l][j] = a_j (1 - 2 l / q)^j (j < 13, zero for j = 13..15) in
 // FP64, split into BF16 hi / lo: [hi | lo], each [l / 8][j / 8][8][16 B].
 __global__ void k_lf_table(int q, int r, const double* __restrict__ a, uint16_t* __restrict__ tab) {
@@ -338,39 +359,35 @@ __global__ void k_lf_table(int q, int r, const double* __restrict__ a, uint16_t*
 }
 
 template <int Q>
-int launch_stage_a(const float2* x, long long nrows, float2* C, const void* tab, int* status, cudaStream_t st) {
+int launch_stage_a(const float2* x, long long nrows, int rows_per_frame, float2* out, const void* tab,
+                   const float2* W, int* status, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     PFT_CUDA_TRY(cudaFuncSetAttribute(k_lf_stage_a<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_A));
     attr = true;
   }
+  const float2* tw = pfth::twiddles(kP);
+  if (!tw) return PFT_ERR_CUDA;
   long long grid = pfth::sm_count();
   if (grid > nrows / 2) grid = nrows / 2;
   if (grid < 1) return PFT_OK;
-  k_lf_stage_a<Q><<<(unsigned)grid, kThreadsA, SMEM_A, st>>>(x, nrows, C, (const uint4*)tab, status);
+  k_lf_stage_a<Q><<<(unsigned)grid, kThreadsA, SMEM_A, st>>>(x, nrows, rows_per_frame, out, (const uint4*)tab, W,
+                                                               tw, status);
   PFT_CUDA_TRY(cudaGetLastError());
   return PFT_OK;
 }
 
-int stage_a(int q, const float2* x, long long nrows, float2* C, const void* tab, int* status, cudaStream_t st) {
+int stage_ab(int q, const float2* x, long long nrows, int rows_per_frame, float2* out, const void* tab,
+             const float2* W, int* status, cudaStream_t st) {
   switch (q) {
-    case 32: return launch_stage_a<32>(x, nrows, C, tab, status, st);
-    case 64: return launch_stage_a<64>(x, nrows, C, tab, status, st);
-    case 128: return launch_stage_a<128>(x, nrows, C, tab, status, st);
-    case 256: return launch_stage_a<256>(x, nrows, C, tab, status, st);
+    case 32: return launch_stage_a<32>(x, nrows, rows_per_frame, out, tab, W, status, st);
+    case 64: return launch_stage_a<64>(x, nrows, rows_per_frame, out, tab, W, status, st);
+    case 128: return launch_stage_a<128>(x, nrows, rows_per_frame, out, tab, W, status, st);
+    case 256: return launch_stage_a<256>(x, nrows, rows_per_frame, out, tab, W, status, st);
     default: return pfth::set_error(PFT_ERR_UNSUPPORTED, "large-frame block length q=%d not built", q);
   }
 }
 
-int stage_b(const float2* C, long long nrows, int rows_per_frame, float2* out, const float2* W, cudaStream_t st) {
-  const float2* tw = pfth::twiddles(kP);
-  if (!tw) return PFT_ERR_CUDA;
-  long long groups = nrows / kRowsB;
-  long long grid = groups < 8LL * pfth::sm_count() ? groups : 8LL * pfth::sm_count();
-  k_lf_stage_b<<<(unsigned)grid, kThreadsB, 0, st>>>(C, nrows, rows_per_frame, out, W, tw);
-  PFT_CUDA_TRY(cudaGetLastError());
-  return PFT_OK;
-}
 
 
 // ============================================================== adjoint
@@ -378,7 +395,7 @@ int stage_b(const float2* C, long long nrows, int rows_per_frame, float2* out, c
 //   H[rho][j] = sum_{t = rho mod 64} conj(W'[t][j]) y[t]
 //   E[k][j]   = sum_rho e^{+2 pi i rho k / 64} H[rho][j]        (F^H)
 //   x[q k + l] = sum_j B[l][j] E[k][j]                         (B real)
-// k_lf_stage_b_adj reads its rows transposed (the layout k_lf_stage_b
+// k_lf_stage_b_adj reads its rows transposed (the layout the forward
 // writes) and produces E[row][j][k]; k_lf_expand expands every block on
 // tensor cores (M = 128 blocks, N = q values l, K = 16 terms j).
 
@@ -389,10 +406,7 @@ __global__ void __launch_bounds__(kThreadsB)
   __shared__ float2 sW[kRt * kMl];
   __shared__ float2 stage[kRowsB][kMl];
   F64::fill(tw, gtw);
-  for (int i = threadIdx.x; i < kRt * kMl; i += blockDim.x) {
-    const int j = i / kMl, sl = i % kMl, l = sl % 32, pos = (sl / 32) >> 1, hi = (sl / 32) & 1;
-    sW[i] = gW[j * kMl + 2 * bitrev<32>(l) + pos + kP * hi];
-  }
+  fill_w_slots(sW, gW);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   typename F64::Net net;
@@ -707,18 +721,14 @@ int lf_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void
   const cudaStream_t st = (cudaStream_t)stream;
   const int n = plan->n1;
   const long long f = plan->lf_chunk;
-  float2* Cw = (float2*)plan->d_ws;
-  float2* TT = Cw + f * (long long)n * kRt * kP;
-  float2* C2 = TT + f * (long long)kMl * n;
+  float2* TT = (float2*)plan->d_ws + f * (long long)n * kRt * kP;  // same place as the adjoint's T^T
   const float2* W = plan->d_W;  // axis 0: W'[j][t_idx], j < RMAX, t_idx < 128
   for (long long f0 = 0; f0 < batch; f0 += f) {
     const long long nf = std::min<long long>(f, batch - f0);
     const float2* xf = (const float2*)x + f0 * (long long)n * n;
     float2* yf = (float2*)y + f0 * (long long)kMl * kMl;
-    int rc = stage_a(plan->q1, xf, nf * n, Cw, plan->d_tc, plan->d_status, st);
-    if (rc == PFT_OK) rc = stage_b(Cw, nf * n, n, TT, W, st);
-    if (rc == PFT_OK) rc = stage_a(plan->q1, TT, nf * kMl, C2, plan->d_tc, plan->d_status, st);
-    if (rc == PFT_OK) rc = stage_b(C2, nf * kMl, kMl, yf, W, st);
+    int rc = stage_ab(plan->q1, xf, nf * n, n, TT, plan->d_tc, W, plan->d_status, st);
+    if (rc == PFT_OK) rc = stage_ab(plan->q1, TT, nf * kMl, kMl, yf, plan->d_tc, W, plan->d_status, st);
     if (rc != PFT_OK) return rc;
   }
   return PFT_OK;
