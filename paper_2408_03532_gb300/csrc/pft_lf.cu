@@ -78,8 +78,6 @@ __device__ __forceinline__ void split_store2(uint8_t* base, uint32_t comp_bytes,
 }
 
 using F64 = Fft<kP>;
-constexpr int kThreadsB = 256;              // stage-B adjoint: one warp per row
-constexpr int kRowsB = kThreadsB / 32;
 
 // W'[j][t_idx] (t_idx < 128) in "slot" order s = (2 pos + hi) 32 + l, where
 // lane l ends the 64-point FFT holding rho = 2 bitrev(l) + pos and owns the
@@ -395,59 +393,9 @@ int stage_ab(int q, const float2* x, long long nrows, int rows_per_frame, float2
 //   H[rho][j] = sum_{t = rho mod 64} conj(W'[t][j]) y[t]
 //   E[k][j]   = sum_rho e^{+2 pi i rho k / 64} H[rho][j]        (F^H)
 //   x[q k + l] = sum_j B[l][j] E[k][j]                         (B real)
-// k_lf_stage_b_adj reads its rows transposed (the layout the forward
-// writes) and produces E[row][j][k]; k_lf_expand expands every block on
+// k_lf_expand reads each row's M inputs transposed (the layout the forward
+// writes), runs the first two steps in its loader warps and the last on
 // tensor cores (M = 128 blocks, N = q values l, K = 16 terms j).
-
-__global__ void __launch_bounds__(kThreadsB)
-    k_lf_stage_b_adj(const float2* __restrict__ in, long long nrows, int rows_per_frame, float2* __restrict__ E,
-                     const float2* __restrict__ gW, const float2* __restrict__ gtw) {
-  __shared__ float2 tw[F64::TAB];
-  __shared__ float2 sW[kRt * kMl];
-  __shared__ float2 stage[kRowsB][kMl];
-  F64::fill(tw, gtw);
-  fill_w_slots(sW, gW);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  typename F64::Net net;
-  F64::init_net(net, lane, tw);
-  for (long long r0 = (long long)blockIdx.x * kRowsB; r0 < nrows; r0 += (long long)gridDim.x * kRowsB) {
-    const long long f = r0 / rows_per_frame;
-    const int rin = (int)(r0 % rows_per_frame);
-    const float2* ip = in + f * (long long)kMl * rows_per_frame + rin;
-    for (int i = threadIdx.x; i < kMl * kRowsB / 2; i += blockDim.x) {
-      const int ti = i / (kRowsB / 2), part = i % (kRowsB / 2);
-      const int r = ti & (kP - 1);
-      const int sl = ((r & 1) * 2 + (ti >> 6)) * 32 + bitrev<32>(r >> 1);
-      const float4 v = __ldg(reinterpret_cast<const float4*>(ip + (long long)ti * rows_per_frame + 2 * part));
-      stage[2 * part][sl] = make_float2(v.x, v.y);
-      stage[2 * part + 1][sl] = make_float2(v.z, v.w);
-    }
-    __syncthreads();
-    const long long row = r0 + warp;
-    float2* dst = E + row * (long long)(kRt * kP);
-#pragma unroll
-    for (int j = 0; j < kRt; ++j) {
-      float2 v[2];
-#pragma unroll
-      for (int pos = 0; pos < 2; ++pos) {
-        float2 h = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int hi = 0; hi < 2; ++hi) {
-          const int sl = (2 * pos + hi) * 32 + lane;
-          const float2 w = sW[j * kMl + sl], yv = stage[warp][sl];
-          h.x = fmaf(w.x, yv.x, fmaf(w.y, yv.y, h.x));   // conj(w) * y
-          h.y = fmaf(w.x, yv.y, fmaf(-w.y, yv.x, h.y));
-        }
-        v[pos] = h;
-      }
-      F64::adj(v, lane, tw, net);  // v[e] = E[lane + 32 e][j]
-      dst[j * kP + lane] = v[0];
-      dst[j * kP + lane + 32] = v[1];
-    }
-    __syncthreads();
-  }
-}
 
 constexpr int kStagesE = 4;
 constexpr uint32_t E_LBO = 16 * CM;               // K-direction step (j 0..7 -> 8..15)
@@ -458,7 +406,9 @@ constexpr uint32_t OFF2_TAB = 0;                  // B^T hi | lo, up to 16 KB
 constexpr uint32_t OFF2_E = 16384;
 constexpr uint32_t OFF2_STG = OFF2_E + kStagesE * E_STAGE;
 constexpr uint32_t STG_BYTES = 4 * 32 * kStgStride * 8;
-constexpr uint32_t OFF2_BAR = OFF2_STG + STG_BYTES;
+constexpr uint32_t OFF2_TW = OFF2_STG + STG_BYTES;
+constexpr uint32_t OFF2_W = OFF2_TW + 160 * 8;
+constexpr uint32_t OFF2_BAR = OFF2_W + kRt * kMl * 8;
 constexpr int NBAR2 = 2 * kStagesE + 2 * 4 + 1;
 constexpr uint32_t OFF2_SLOT = OFF2_BAR + 8 * NBAR2;
 constexpr uint32_t OFF2_ABORT = OFF2_SLOT + 8;
@@ -467,11 +417,28 @@ static_assert(SMEM_E <= 232448, "shared memory layout too large");
 constexpr int kLdWarpsE = 4, kLdWarp0E = 8;
 constexpr int kThreadsE = 32 * (kLdWarp0E + kLdWarpsE);  // warps 5-7 idle
 
-// x[row][q k + l] = sum_j B[l][j] E[row][j][k]; tile t = rows 2t, 2t + 1.
+__device__ __forceinline__ void split8_store(uint8_t* hi_base, uint32_t comp_bytes, uint32_t off, const float (&v)[8]) {
+  __nv_bfloat162 h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(h[i]);
+    l[i] = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+  }
+  *reinterpret_cast<uint4*>(hi_base + off) = *reinterpret_cast<uint4*>(h);
+  *reinterpret_cast<uint4*>(hi_base + comp_bytes + off) = *reinterpret_cast<uint4*>(l);
+}
+
+// The adjoint of one axis for `nrows` rows, read transposed from
+// in[frame][t_idx][row in frame]: the loader warps run the stage-B adjoint of
+// two rows per tile (warp pair per row, j = 0..7 and 8..15) straight into the
+// BF16 operand of the tensor-core expansion
+//   x[row][q k + l] = sum_j B[l][j] E[row][k][j].
 template <int Q>
 __global__ void __launch_bounds__(kThreadsE, 1)
-    k_lf_expand(const float2* __restrict__ E, long long nrows, float2* __restrict__ x,
-                const uint4* __restrict__ tab, int* status) {
+    k_lf_expand(const float2* __restrict__ in, long long nrows, int rows_per_frame, float2* __restrict__ x,
+                const uint4* __restrict__ tab, const float2* __restrict__ gW, const float2* __restrict__ gtw,
+                int* status) {
   constexpr int N = kP * Q;
   constexpr uint32_t T_LBO = (Q / 8) * CM;         // B^T: [j / 8][l / 8][8][16 B]
   constexpr uint32_t T_HALF = 2 * T_LBO;
@@ -491,6 +458,10 @@ __global__ void __launch_bounds__(kThreadsE, 1)
 
   for (int i = threadIdx.x; i < (int)(2 * T_HALF / 16); i += blockDim.x)
     reinterpret_cast<uint4*>(sm + OFF2_TAB)[i] = __ldg(tab + i);
+  float2* s_tw = reinterpret_cast<float2*>(sm + OFF2_TW);
+  float2* s_w = reinterpret_cast<float2*>(sm + OFF2_W);
+  F64::fill(s_tw, gtw);
+  fill_w_slots(s_w, gW);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesE; ++s) {
       mbar_init(E_FULL + 8 * s, kLdWarpsE);
@@ -583,29 +554,51 @@ __global__ void __launch_bounds__(kThreadsE, 1)
       }
     }
   } else if (warp >= kLdWarp0E) {
-    // item i: j pair jp = word + 4 (i & 1), block m = (4 w + (i >> 1)) 8 + mb
-    const int w = warp - kLdWarp0E, word = lane >> 3, mb = lane & 7;
+    // warp pair per row r of the tile; warp h fills the K core-matrix column
+    // j = 8h .. 8h + 7 of blocks k = lane and lane + 32 (terms j >= 13 are 0)
+    const int w = warp - kLdWarp0E, r = w >> 1, h = w & 1;
+    typename F64::Net net;
+    F64::init_net(net, lane, s_tw);
+    const int rho0 = 2 * bitrev<32>(lane);
     for (long long T = 0; T < ntiles; ++T) {
       const long long tile = blockIdx.x + T * gridDim.x;
       const int s = (int)(T % kStagesE);
       const uint32_t u = (uint32_t)(T / kStagesE);
-      float2 va[8], vb[8];
+      const long long row = 2 * tile + r;
+      const long long f = row / rows_per_frame, rin = row % rows_per_frame;
+      const float2* ip = in + f * (long long)kMl * rows_per_frame + rin;
+      float2 yv[4];  // slot i * 32 + lane: t_idx = rho0 + (i >> 1) + 64 (i & 1)
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int jp = word + 4 * (i & 1), m = (4 * w + (i >> 1)) * 8 + mb;
-        const float2* src = E + (2 * tile + (m >> 6)) * (long long)(kRt * kP) + (m & 63);
-        va[i] = 2 * jp < kRt ? __ldg(src + 2 * jp * kP) : make_float2(0.f, 0.f);
-        vb[i] = 2 * jp + 1 < kRt ? __ldg(src + (2 * jp + 1) * kP) : make_float2(0.f, 0.f);
+      for (int i = 0; i < 4; ++i) yv[i] = __ldg(ip + (long long)(rho0 + (i >> 1) + kP * (i & 1)) * rows_per_frame);
+      float er0[8], ei0[8], er1[8], ei1[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = 8 * h + jj;
+        float2 hv[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (j < kRt) {
+#pragma unroll
+          for (int pos = 0; pos < 2; ++pos) {
+#pragma unroll
+            for (int hi = 0; hi < 2; ++hi) {
+              const float2 wv = s_w[j * kMl + (2 * pos + hi) * 32 + lane], yy = yv[2 * pos + hi];
+              hv[pos].x = fmaf(wv.x, yy.x, fmaf(wv.y, yy.y, hv[pos].x));   // conj(W') y
+              hv[pos].y = fmaf(wv.x, yy.y, fmaf(-wv.y, yy.x, hv[pos].y));
+            }
+          }
+          F64::adj(hv, lane, s_tw, net);  // hv[e] = E[lane + 32 e][j]
+        }
+        er0[jj] = hv[0].x;
+        ei0[jj] = hv[0].y;
+        er1[jj] = hv[1].x;
+        ei1[jj] = hv[1].y;
       }
       if (!mbar_wait(E_EMPTY + 8 * s, (u & 1u) ^ 1u, abort_flag, kWaitNs)) break;
       uint8_t* es = sm + OFF2_E + s * E_STAGE;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int jp = word + 4 * (i & 1), m = (4 * w + (i >> 1)) * 8 + mb;
-        const uint32_t off = (uint32_t)(jp >> 2) * E_LBO + (uint32_t)m * 16 + (uint32_t)(jp & 3) * 4;
-        split_store2(es, E_COMP, off, va[i].x, vb[i].x);
-        split_store2(es + 2 * E_COMP, E_COMP, off, va[i].y, vb[i].y);
-      }
+      const uint32_t m0 = (uint32_t)(64 * r + lane), m1 = m0 + 32;
+      split8_store(es, E_COMP, (uint32_t)h * E_LBO + m0 * 16, er0);
+      split8_store(es + 2 * E_COMP, E_COMP, (uint32_t)h * E_LBO + m0 * 16, ei0);
+      split8_store(es, E_COMP, (uint32_t)h * E_LBO + m1 * 16, er1);
+      split8_store(es + 2 * E_COMP, E_COMP, (uint32_t)h * E_LBO + m1 * 16, ei1);
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(E_FULL + 8 * s);
@@ -641,7 +634,8 @@ __global__ void k_lf_table_adj(int q, int r, const double* __restrict__ a, uint1
 }
 
 template <int Q>
-int launch_expand(const float2* E, long long nrows, float2* x, const void* tab, int* status, cudaStream_t st) {
+int launch_expand(const float2* in, long long nrows, int rows_per_frame, float2* x, const void* tab, const float2* W,
+                  int* status, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     PFT_CUDA_TRY(cudaFuncSetAttribute(k_lf_expand<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_E));
@@ -650,30 +644,25 @@ int launch_expand(const float2* E, long long nrows, float2* x, const void* tab, 
   long long grid = pfth::sm_count();
   if (grid > nrows / 2) grid = nrows / 2;
   if (grid < 1) return PFT_OK;
-  k_lf_expand<Q><<<(unsigned)grid, kThreadsE, SMEM_E, st>>>(E, nrows, x, (const uint4*)tab, status);
+  const float2* tw = pfth::twiddles(kP);
+  if (!tw) return PFT_ERR_CUDA;
+  k_lf_expand<Q><<<(unsigned)grid, kThreadsE, SMEM_E, st>>>(in, nrows, rows_per_frame, x, (const uint4*)tab, W, tw,
+                                                              status);
   PFT_CUDA_TRY(cudaGetLastError());
   return PFT_OK;
 }
 
-int expand(int q, const float2* E, long long nrows, float2* x, const void* tab, int* status, cudaStream_t st) {
+int expand(int q, const float2* in, long long nrows, int rows_per_frame, float2* x, const void* tab, const float2* W,
+           int* status, cudaStream_t st) {
   switch (q) {
-    case 32: return launch_expand<32>(E, nrows, x, tab, status, st);
-    case 64: return launch_expand<64>(E, nrows, x, tab, status, st);
-    case 128: return launch_expand<128>(E, nrows, x, tab, status, st);
-    case 256: return launch_expand<256>(E, nrows, x, tab, status, st);
+    case 32: return launch_expand<32>(in, nrows, rows_per_frame, x, tab, W, status, st);
+    case 64: return launch_expand<64>(in, nrows, rows_per_frame, x, tab, W, status, st);
+    case 128: return launch_expand<128>(in, nrows, rows_per_frame, x, tab, W, status, st);
+    case 256: return launch_expand<256>(in, nrows, rows_per_frame, x, tab, W, status, st);
     default: return pfth::set_error(PFT_ERR_UNSUPPORTED, "large-frame block length q=%d not built", q);
   }
 }
 
-int stage_b_adj(const float2* in, long long nrows, int rows_per_frame, float2* E, const float2* W, cudaStream_t st) {
-  const float2* tw = pfth::twiddles(kP);
-  if (!tw) return PFT_ERR_CUDA;
-  long long groups = nrows / kRowsB;
-  long long grid = groups < 8LL * pfth::sm_count() ? groups : 8LL * pfth::sm_count();
-  k_lf_stage_b_adj<<<(unsigned)grid, kThreadsB, 0, st>>>(in, nrows, rows_per_frame, E, W, tw);
-  PFT_CUDA_TRY(cudaGetLastError());
-  return PFT_OK;
-}
 
 }  // namespace
 
@@ -700,11 +689,12 @@ int lf_build(pft_plan* plan) {
   PFT_CUDA_TRY(cudaGetLastError());
   PFT_CUDA_TRY(cudaDeviceSynchronize());
   PFT_CUDA_TRY(cudaFree(d_a));
-  // frames per chunk: keep the stage-A intermediate of a chunk near 128 MB (L2-sized)
-  const long long c_bytes = (long long)n * kRt * kP * sizeof(float2);
-  plan->lf_chunk = (int)std::max(1LL, (128LL << 20) / c_bytes);
+  // frames per pass: the transposed intermediate T^T (128 x n per frame) of a
+  // pass stays well inside L2
+  const long long t_bytes = (long long)kMl * n * sizeof(float2);
+  plan->lf_chunk = (int)std::max(1LL, (32LL << 20) / t_bytes);
   const long long f = plan->lf_chunk;
-  const size_t ws = (size_t)f * ((size_t)n * kRt * kP + (size_t)kMl * n + (size_t)kMl * kRt * kP) * sizeof(float2);
+  const size_t ws = (size_t)f * (size_t)kMl * n * sizeof(float2);
   PFT_CUDA_TRY(cudaMalloc(&plan->d_ws, ws));
   PFT_CUDA_TRY(cudaHostAlloc(&plan->h_status, sizeof(int), cudaHostAllocMapped));
   *plan->h_status = PFT_OK;
@@ -721,7 +711,7 @@ int lf_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void
   const cudaStream_t st = (cudaStream_t)stream;
   const int n = plan->n1;
   const long long f = plan->lf_chunk;
-  float2* TT = (float2*)plan->d_ws + f * (long long)n * kRt * kP;  // same place as the adjoint's T^T
+  float2* TT = (float2*)plan->d_ws;
   const float2* W = plan->d_W;  // axis 0: W'[j][t_idx], j < RMAX, t_idx < 128
   for (long long f0 = 0; f0 < batch; f0 += f) {
     const long long nf = std::min<long long>(f, batch - f0);
@@ -743,18 +733,14 @@ int lf_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void
   const cudaStream_t st = (cudaStream_t)stream;
   const int n = plan->n1;
   const long long f = plan->lf_chunk;
-  float2* Ew = (float2*)plan->d_ws;
-  float2* TT = Ew + f * (long long)n * kRt * kP;
-  float2* E2 = TT + f * (long long)kMl * n;
+  float2* TT = (float2*)plan->d_ws;
   const float2* W = plan->d_W;
   for (long long f0 = 0; f0 < batch; f0 += f) {
     const long long nf = std::min<long long>(f, batch - f0);
     const float2* yf = (const float2*)y + f0 * (long long)kMl * kMl;
     float2* xf = (float2*)x + f0 * (long long)n * n;
-    int rc = stage_b_adj(yf, nf * kMl, kMl, E2, W, st);
-    if (rc == PFT_OK) rc = expand(plan->q1, E2, nf * kMl, TT, plan->d_tc_adj, plan->d_status, st);
-    if (rc == PFT_OK) rc = stage_b_adj(TT, nf * n, n, Ew, W, st);
-    if (rc == PFT_OK) rc = expand(plan->q1, Ew, nf * n, xf, plan->d_tc_adj, plan->d_status, st);
+    int rc = expand(plan->q1, yf, nf * kMl, kMl, TT, plan->d_tc_adj, W, plan->d_status, st);
+    if (rc == PFT_OK) rc = expand(plan->q1, TT, nf * n, n, xf, plan->d_tc_adj, W, plan->d_status, st);
     if (rc != PFT_OK) return rc;
   }
   return PFT_OK;

@@ -60,16 +60,18 @@ def test_structured_frames_and_exact_transform(env):
 
 
 def test_chunked_batch_matches_single_frames(env):
-    """More frames than one workspace pass holds: every frame equals the same
-    frame transformed alone."""
+    """More frames than one workspace pass holds: every frame's forward and
+    adjoint equal the same frame transformed alone."""
     torch, pft = env
     n = 2048
     plan = pft.Plan(n, M, precision=pft.PREC_SPLIT_BF16)
-    B = 11
+    B = 33  # a pass holds 15 frames of 2048^2
     x = torch.randn(B, n, n, dtype=torch.complex64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
     y = plan.forward(x)
-    for f in (0, 4, 9, 10):
+    xa = plan.adjoint(y)
+    for f in (0, 14, 15, 31, 32):
         assert torch.equal(plan.forward(x[f:f + 1]), y[f:f + 1])
+        assert torch.equal(plan.adjoint(y[f:f + 1]), xa[f:f + 1])
 
 
 @pytest.mark.parametrize("n,batch", [(2048, 3), (4096, 1), (8192, 1)])
