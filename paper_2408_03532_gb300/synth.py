@@ -163,14 +163,18 @@ def small_raster_problem(noise: bool = False) -> dict:
 
 
 def spiral_problem(side: int = 1024, n: int = 128, count: int = 3600,
-                   peak_photons: float | None = 1e4, M: int = 32) -> dict:
-    """Fermat-spiral reconstruction (default: 1024^2 object, 128^2 probe, 3600 positions)."""
-    obj = make_object(side)
+                   peak_photons: float | None = 1e4, M: int = 32, seed_shift: int = 0) -> dict:
+    """Fermat-spiral reconstruction (default: 1024^2 object, 128^2 probe, 3600 positions).
+
+    ``seed_shift`` draws another instance of the same recipe (object, scan
+    jitter, Poisson noise and start move by the shift; the probe is the
+    instrument and stays)."""
+    obj = make_object(side, seed=SEED_OBJECT + seed_shift)
     probe = make_probe(n)
-    pos = fermat_scan(side, n, count)
-    inten = simulate_intensities(obj, probe, pos, peak_photons)
+    pos = fermat_scan(side, n, count, seed=SEED_SCAN + seed_shift)
+    inten = simulate_intensities(obj, probe, pos, peak_photons, seed=SEED_POISSON + seed_shift)
     return dict(obj=obj, probe=probe, pos=pos, intensities=inten, M=M,
-                init=random_init(side))
+                init=random_init(side, seed=SEED_INIT + seed_shift))
 
 
 def gradient_problem() -> dict:
