@@ -357,7 +357,7 @@ def main() -> None:
     # time to target: plain full-FFT PIE vs the hybrid, from the same start
     ttt = None
     if not args.no_ttt:
-        ttt = time_to_target(ctx, P, probe, pft, synth, torch, init, truth, args, stream, dev)
+        ttt = time_to_target(ctx, pft, synth, torch, init, truth, args, stream, dev)
 
     pft_batch = None if args.no_pft_batch else measure_pft_batch(pft, torch, dev, stream, flush, args.pft_frames)
     batch64 = None if args.no_batch64 else measure_batch64(pft, synth, torch, dev, stream, flush)
@@ -605,21 +605,21 @@ def measure_batch64(pft, synth, torch, dev, stream, flush, reps: int = 3) -> dic
 HYBRID_GRID = [(k, beta) for k in (1, 2, 3) for beta in (0.25, 0.5, 1.0)]
 
 
-def _trajectory(phases, z0, truth, judge, pft, torch, stream):
-    """Runs (context, transform, beta, sweeps) phases from z0; each sweep is
-    timed on the GPU (CUDA events, statistics included); the phase-aligned
-    NRMSE after it (judge's mask) is measured but not timed."""
+def _trajectory(ctx, phases, z0, truth, pft, torch, stream):
+    """Runs (transform, mode, beta, sweeps) phases from z0 on one context; each
+    sweep is timed on the GPU (CUDA events, statistics included); the
+    phase-aligned NRMSE after it is measured but not timed."""
     z = z0.clone()
     t, out = 0.0, []
-    for ctx, transform, beta, count in phases:
+    for transform, mode, beta, count in phases:
         for _ in range(count):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            ctx.iteration(z, transform, beta, stats=True)
+            ctx.iteration(z, transform, beta, stats=True, mode=mode)
             b.record(stream)
             torch.cuda.synchronize()
             t += a.elapsed_time(b) / 1e3
-            out.append((t, judge.nrmse(z, truth), "pft" if transform == pft.TRANSFORM_PFT else "full"))
+            out.append((t, ctx.nrmse(z, truth), "pft" if transform == pft.TRANSFORM_PFT else "full"))
     return out
 
 
@@ -630,23 +630,22 @@ def _first(run, x):
     return None, None
 
 
-def time_to_target(ctx, P, probe, pft, synth, torch, init, truth, args, stream, dev) -> dict:
+def time_to_target(ctx, pft, synth, torch, init, truth, args, stream, dev) -> dict:
     """Plain full-FFT PIE against PFT-warm-started PIE (Algorithm 3) from the same
     start, each as a trajectory of GPU-timed sweeps.
 
     * configured: 20 PFT sweeps in the context's mode, then full sweeps;
     * tuned: Algorithm 3 with the PFT phase in batched mode (one launch per
-      sweep, all positions read the same object) for k sweeps with step beta,
-      then coloured full sweeps. (k, beta) is chosen on a separate instance of
+      sweep, all positions read the same object; pie_iteration_mode) for k
+      sweeps with step beta, then coloured full sweeps. (k, beta) is chosen on a separate instance of
       the same recipe (other object, scan jitter, noise and start seeds) as the
       schedule that first reaches 1.01 x that instance's plain best NRMSE, and
       only then run on the benchmark instance.
     Reports, for several targets, the first time each run reaches them."""
     mx = args.ttt_max_sweeps
-    full = pft.TRANSFORM_FULL
-    plain = _trajectory([(ctx, full, 1.0, mx)], init, truth, ctx, pft, torch, stream)
-    hyb = _trajectory([(ctx, pft.TRANSFORM_PFT, 1.0, 20), (ctx, full, 1.0, mx)], init, truth, ctx, pft, torch,
-                      stream)
+    full, pftt, col, bat = pft.TRANSFORM_FULL, pft.TRANSFORM_PFT, pft.MODE_COLOURED, pft.MODE_BATCHED
+    plain = _trajectory(ctx, [(full, col, 1.0, mx)], init, truth, pft, torch, stream)
+    hyb = _trajectory(ctx, [(pftt, col, 1.0, 20), (full, col, 1.0, mx)], init, truth, pft, torch, stream)
     # choose the tuned schedule on another instance
     T = synth.spiral_problem(seed_shift=100)
     n_t = T["probe"].shape[0]
@@ -655,29 +654,22 @@ def time_to_target(ctx, P, probe, pft, synth, torch, init, truth, args, stream, 
     truth_t = torch.from_numpy(T["obj"].astype(np.complex64)).to(dev)
     init_t = torch.from_numpy(T["init"].astype(np.complex64)).to(dev)
     shape_t = T["obj"].shape
-    col_t = pft.PieContext(shape_t, probe_t, T["pos"], inten_t, M=T["M"], mode=pft.MODE_COLOURED)
-    bat_t = pft.PieContext(shape_t, probe_t, T["pos"], inten_t, M=T["M"], mode=pft.MODE_BATCHED)
+    ctx_t = pft.PieContext(shape_t, probe_t, T["pos"], inten_t, M=T["M"], mode=col)
     del inten_t
     nsw = 12
-    plain_t = _trajectory([(col_t, full, 1.0, nsw)], init_t, truth_t, col_t, pft, torch, stream)
+    plain_t = _trajectory(ctx_t, [(full, col, 1.0, nsw)], init_t, truth_t, pft, torch, stream)
     goal_t = 1.01 * min(e for _, e, _ in plain_t)
     tuning = []
     for k, beta in HYBRID_GRID:
-        run = _trajectory([(bat_t, pft.TRANSFORM_PFT, beta, k), (col_t, full, 1.0, nsw)], init_t, truth_t, col_t,
-                          pft, torch, stream)
+        run = _trajectory(ctx_t, [(pftt, bat, beta, k), (full, col, 1.0, nsw)], init_t, truth_t, pft, torch,
+                          stream)
         tuning.append((_first(run, goal_t)[0], k, beta))
-    col_t.close()
-    bat_t.close()
+    ctx_t.close()
     reached = [x for x in tuning if x[0] is not None]
     t_plain_t = _first(plain_t, goal_t)[0]
     k_best, beta_best = (min(reached)[1:] if reached else (1, 0.5))
-    # the chosen schedule on the benchmark instance (batched PFT context of the same problem)
-    inten = torch.from_numpy(P["intensities"].astype(np.float32)).to(dev)
-    bat = pft.PieContext(tuple(truth.shape), probe, P["pos"], inten, M=P["M"], mode=pft.MODE_BATCHED)
-    del inten
-    tuned = _trajectory([(bat, pft.TRANSFORM_PFT, beta_best, k_best), (ctx, full, 1.0, mx)], init, truth, ctx, pft,
-                        torch, stream)
-    bat.close()
+    # the chosen schedule on the benchmark instance
+    tuned = _trajectory(ctx, [(pftt, bat, beta_best, k_best), (full, col, 1.0, mx)], init, truth, pft, torch, stream)
     best = min(e for _, e, _ in plain)
     targets = [("config", args.target_nrmse), ("plain_best_x1.01", best * 1.01), ("0.2", 0.2), ("0.3", 0.3)]
     res = {}

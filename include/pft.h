@@ -213,6 +213,13 @@ int pie_ctx_colours(const pie_ctx* ctx, int* ncolours, int32_t* colour_of);
 int pie_iteration(pie_ctx* ctx, void* object, int transform, double beta,
                   pie_stats* stats, void* stream);
 
+/* pie_iteration in the given mode (PIE_MODE_COLOURED or PIE_MODE_BATCHED)
+ * whatever the context was created with; the batched step divides by the
+ * context's illumination as in batched contexts. A batched sweep on a
+ * coloured context allocates one object-sized accumulator on first use. */
+int pie_iteration_mode(pie_ctx* ctx, void* object, int transform, int mode, double beta,
+                       pie_stats* stats, void* stream);
+
 /* Blind PIE (Eq. pie_update with Eq. epie_probe_update), coloured mode only:
  * one sweep that also refines the context's probe. Within a colour every
  * position uses the probe of the colour's start and updates its patch; the
@@ -242,6 +249,9 @@ typedef struct pie_schedule {
   int max_pft, max_full;
   double tv_pft, tv_full;  /* TV weights (0 = none): one pie_tv_step after each sweep */
   double tv_eps;           /* TV smoothing (0 = 1e-3)                                 */
+  int pft_batched;         /* 1: PFT phase in PIE_MODE_BATCHED (one launch per sweep,
+                              all positions read the same object), full phase in the
+                              context's mode; 0: both phases in the context's mode   */
 } pie_schedule;
 
 typedef struct pie_trace {

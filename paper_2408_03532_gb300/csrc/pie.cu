@@ -262,6 +262,7 @@ struct pie_ctx {
     double beta;
     double gamma;  // < 0: non-blind
     bool stats;
+    int mode;      // PIE_MODE_* of the sweep
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;
@@ -395,7 +396,7 @@ int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) 
 }
 
 int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st,
-                  double gamma = -1.0);
+                  double gamma = -1.0, int mode = -1);
 
 __global__ void k_fill(float2* __restrict__ z, long long n, float2 v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -626,8 +627,9 @@ namespace {
 // (or the batched kernel and its update), and with `stats` the FP64 norms and
 // their copy to pinned host memory.
 int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st,
-                  double gamma) {
+                  double gamma, int mode) {
   const long long HW = (long long)c->H * c->W;
+  if (mode < 0) mode = c->pb.mode;
   const bool blind = gamma >= 0.0;
   const int n2i = c->n * c->n;
   if (stats) PFT_CUDA_TRY(cudaMemcpyAsync(c->d_prev, obj, sizeof(float2) * HW, cudaMemcpyDeviceToDevice, st));
@@ -644,7 +646,7 @@ int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stat
   a.dat = transform == PIE_TRANSFORM_PFT ? c->d_ampc : c->d_amp;
   a.gprobe = nullptr;
   a.red = c->d_red;
-  if (c->pb.mode == PIE_MODE_COLOURED) {
+  if (mode == PIE_MODE_COLOURED) {
     a.coef = (float)(beta / ((double)c->probe_max2 * n2));
     a.acc = nullptr;
     if (blind) {
@@ -688,14 +690,15 @@ int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stat
 
 // Returns the executable graph of a sweep, capturing it on first use.
 int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaGraphExec_t* out,
-                double gamma = -1.0) {
+                double gamma, int mode) {
   for (auto& g : c->graphs)
-    if (g.obj == obj && g.transform == transform && g.beta == beta && g.stats == stats && g.gamma == gamma) {
+    if (g.obj == obj && g.transform == transform && g.beta == beta && g.stats == stats && g.gamma == gamma &&
+        g.mode == mode) {
       *out = g.exec;
       return PFT_OK;
     }
   PFT_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_sweep(c, obj, transform, beta, stats, c->cap_stream, gamma);
+  int rc = enqueue_sweep(c, obj, transform, beta, stats, c->cap_stream, gamma, mode);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   if (rc != PFT_OK) {
@@ -711,20 +714,26 @@ int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats,
     cudaGraphExecDestroy(c->graphs.front().exec);
     c->graphs.erase(c->graphs.begin());
   }
-  c->graphs.push_back({obj, transform, beta, gamma, stats, exec});
+  c->graphs.push_back({obj, transform, beta, gamma, stats, mode, exec});
   *out = exec;
   return PFT_OK;
 }
 
-int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, pie_stats* stats, void* stream) {
+int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, pie_stats* stats, void* stream,
+            int mode = -1) {
   if (!c || !object) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (mode < 0) mode = c->pb.mode;
+  if (mode != PIE_MODE_COLOURED && mode != PIE_MODE_BATCHED)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown mode %d", mode);
+  if (mode == PIE_MODE_BATCHED && !c->d_acc)
+    PFT_CUDA_TRY(cudaMalloc(&c->d_acc, sizeof(float2) * (size_t)c->H * c->W));
   if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
     return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
   if (transform == PIE_TRANSFORM_FULL && !c->have_full)
     return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n in {16, 32, 64, 128}, not %d", c->n);
   cudaStream_t st = (cudaStream_t)stream;
   if (gamma >= 0.0) {
-    if (c->pb.mode != PIE_MODE_COLOURED)
+    if (mode != PIE_MODE_COLOURED)
       return pfth::set_error(PFT_ERR_UNSUPPORTED, "blind PIE runs in coloured mode");
     const size_t n2 = (size_t)c->n * c->n;
     if (!c->d_pacc) PFT_CUDA_TRY(cudaMalloc(&c->d_pacc, sizeof(float2) * n2));
@@ -732,7 +741,7 @@ int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, 
     if (!c->d_pscale) PFT_CUDA_TRY(cudaMalloc(&c->d_pscale, sizeof(float)));
   }
   cudaGraphExec_t exec = nullptr;
-  int rc = sweep_graph(c, (float2*)object, transform, beta, stats != nullptr, &exec, gamma);
+  int rc = sweep_graph(c, (float2*)object, transform, beta, stats != nullptr, &exec, gamma, mode);
   if (rc != PFT_OK) return rc;
   PFT_CUDA_TRY(cudaGraphLaunch(exec, st));
   if (stats) {
@@ -752,6 +761,11 @@ extern "C" {
 
 int pie_iteration(pie_ctx* c, void* object, int transform, double beta, pie_stats* stats, void* stream) {
   return iterate(c, object, transform, beta, -1.0, stats, stream);
+}
+
+int pie_iteration_mode(pie_ctx* c, void* object, int transform, int mode, double beta, pie_stats* stats,
+                       void* stream) {
+  return iterate(c, object, transform, beta, -1.0, stats, stream, mode);
 }
 
 int pie_iteration_blind(pie_ctx* c, void* object, int transform, double beta, double gamma, pie_stats* stats,
@@ -841,9 +855,10 @@ int warm_start_then_refine(pie_ctx* c, void* object, const pie_schedule* s, cons
   if (ntrace) *ntrace = 0;
   const auto t0 = std::chrono::steady_clock::now();
   int cnt = 0;
-  const struct { int tr; double beta, tol; int mx; double tv; } phases[2] = {
-      {PIE_TRANSFORM_PFT, s->beta_pft, s->tol_pft, s->max_pft, s->tv_pft},
-      {PIE_TRANSFORM_FULL, s->beta_full, s->tol_full, s->max_full, s->tv_full}};
+  const struct { int tr; double beta, tol; int mx; double tv; int mode; } phases[2] = {
+      {PIE_TRANSFORM_PFT, s->beta_pft, s->tol_pft, s->max_pft, s->tv_pft,
+       s->pft_batched ? PIE_MODE_BATCHED : c->pb.mode},
+      {PIE_TRANSFORM_FULL, s->beta_full, s->tol_full, s->max_full, s->tv_full, c->pb.mode}};
   cudaStream_t st = (cudaStream_t)stream;
   const long long HW = (long long)c->H * c->W;
   for (const auto& ph : phases) {
@@ -853,7 +868,7 @@ int warm_start_then_refine(pie_ctx* c, void* object, const pie_schedule* s, cons
       pie_stats stt;
       if (ph.tv > 0.0)
         PFT_CUDA_TRY(cudaMemcpyAsync(c->d_start, object, sizeof(float2) * HW, cudaMemcpyDeviceToDevice, st));
-      int rc = pie_iteration(c, object, ph.tr, ph.beta, &stt, stream);
+      int rc = pie_iteration_mode(c, object, ph.tr, ph.mode, ph.beta, &stt, stream);
       if (rc != PFT_OK) return rc;
       if (ph.tv > 0.0) {
         // one TV gradient step after the sweep; the stopping rule sees the regularised object

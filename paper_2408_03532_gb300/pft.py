@@ -58,7 +58,8 @@ class PieStats(ctypes.Structure):
 class PieSchedule(ctypes.Structure):
     _fields_ = [("beta_pft", ctypes.c_double), ("beta_full", ctypes.c_double), ("tol_pft", ctypes.c_double),
                 ("tol_full", ctypes.c_double), ("max_pft", ctypes.c_int), ("max_full", ctypes.c_int),
-                ("tv_pft", ctypes.c_double), ("tv_full", ctypes.c_double), ("tv_eps", ctypes.c_double)]
+                ("tv_pft", ctypes.c_double), ("tv_full", ctypes.c_double), ("tv_eps", ctypes.c_double),
+                ("pft_batched", ctypes.c_int)]
 
 
 class PieTrace(ctypes.Structure):
@@ -104,6 +105,7 @@ def load() -> ctypes.CDLL:
         "pie_ctx_colours": (ctypes.c_int, [_P, _P, _P]),
         "pie_ctx_info_get": (ctypes.c_int, [_P, _P]),
         "pie_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
+        "pie_iteration_mode": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P]),
         "pie_iteration_blind": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P]),
         "pie_ctx_probe": (ctypes.c_int, [_P, _P, _P]),
         "pie_ctx_set_probe": (ctypes.c_int, [_P, _P, _P]),
@@ -279,6 +281,7 @@ class Schedule:
     tv_pft: float = 0.0
     tv_full: float = 0.0
     tv_eps: float = 1e-3
+    pft_batched: bool = False
 
 
 class PieContext:
@@ -315,11 +318,16 @@ class PieContext:
         import torch
         _need(obj, torch.complex64, self.shape, name)
 
-    def iteration(self, obj, transform: int = TRANSFORM_PFT, beta: float = 1.0, stats: bool = True, stream=None):
+    def iteration(self, obj, transform: int = TRANSFORM_PFT, beta: float = 1.0, stats: bool = True, stream=None,
+                  mode: int | None = None):
+        """One sweep; `mode` (MODE_COLOURED / MODE_BATCHED) overrides the context's."""
         self._obj(obj)
         st = PieStats()
-        _check(load().pie_iteration(self._h, _ptr(obj), transform, beta,
-                                    ctypes.byref(st) if stats else None, _stream(stream)))
+        sp = ctypes.byref(st) if stats else None
+        if mode is None:
+            _check(load().pie_iteration(self._h, _ptr(obj), transform, beta, sp, _stream(stream)))
+        else:
+            _check(load().pie_iteration_mode(self._h, _ptr(obj), transform, mode, beta, sp, _stream(stream)))
         return {"phi": st.phi, "rel_change": st.rel_change} if stats else None
 
     def tv_step(self, obj, lam: float, eps: float = 1e-3, stream=None):
@@ -369,7 +377,8 @@ class PieContext:
         if truth is not None:
             self._obj(truth, "truth")
         s = PieSchedule(schedule.beta_pft, schedule.beta_full, schedule.tol_pft, schedule.tol_full,
-                        schedule.max_pft, schedule.max_full, schedule.tv_pft, schedule.tv_full, schedule.tv_eps)
+                        schedule.max_pft, schedule.max_full, schedule.tv_pft, schedule.tv_full, schedule.tv_eps,
+                        int(schedule.pft_batched))
         cap = max(1, schedule.max_pft + schedule.max_full)
         tr = (PieTrace * cap)()
         cnt = ctypes.c_int()

@@ -96,6 +96,50 @@ def test_batched_sweep_matches_oracle(env, small, transform):
     assert st["phi"] == pytest.approx(phi, rel=TOL)
 
 
+@pytest.mark.parametrize("transform", ["pft", "full"])
+def test_batched_mode_on_coloured_context(env, small, transform):
+    """pie_iteration_mode: a batched sweep requested from a coloured context is
+    the oracle's batched sweep."""
+    torch, pft = env
+    P = small
+    ctx = make_ctx(P, torch, pft)
+    z = c64(P["init"], torch)
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    st = ctx.iteration(z, tr, 0.7, mode=pft.MODE_BATCHED)
+    T, d = oracle_T(P, transform)
+    zo, phi = opie.batched_sweep(P["init"], P["probe"], P["pos"], d, T, 0.7, delta_rel=1e-3)
+    assert rel(z.cpu().numpy(), zo) < TOL
+    assert st["phi"] == pytest.approx(phi, rel=TOL)
+
+
+def test_hybrid_with_batched_pft_phase_matches_oracle(env, small):
+    """Algorithm 3 with the PFT phase in batched mode (schedule.pft_batched):
+    2 batched PFT sweeps, then 3 coloured full sweeps, against the oracle's
+    batched and colour-major sweeps."""
+    torch, pft = env
+    P = small
+    ctx = make_ctx(P, torch, pft)
+    z = c64(P["init"], torch)
+    truth = c64(P["obj"], torch)
+    sched = pft.Schedule(0.5, 1.0, 0.0, 0.0, 2, 3, pft_batched=True)
+    tr = ctx.warm_start_then_refine(z, sched, truth)
+    assert [t["phase"] for t in tr] == ["pft"] * 2 + ["full"] * 3
+    Tp, dc = oracle_T(P, "pft")
+    Tf, d = oracle_T(P, "full")
+    order = opie.colour_major_order(opie.greedy_colouring(P["pos"], 32, 32))
+    mask = opie.illuminated_mask(P["probe"], P["pos"], P["obj"].shape)
+    zo, errs = P["init"], []
+    for _ in range(2):
+        zo, _ = opie.batched_sweep(zo, P["probe"], P["pos"], dc, Tp, 0.5, delta_rel=1e-3)
+        errs.append(opie.nrmse(zo, P["obj"], mask))
+    for _ in range(3):
+        zo, _ = opie.pie_sweep(zo, P["probe"], P["pos"], d, Tf, 1.0, order)
+        errs.append(opie.nrmse(zo, P["obj"], mask))
+    for g, o in zip(tr, errs):
+        assert abs(g["nrmse"] - o) < 1e-4
+    assert rel(z.cpu().numpy(), zo) < 1e-4
+
+
 def test_hybrid_trajectory_matches_oracle(env, small):
     """Algorithm 3 with 10 PFT and 10 full sweeps: the per-sweep error of the GPU
     run stays within 1e-4 of the oracle's in the same (colour-major) order."""
