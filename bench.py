@@ -443,8 +443,8 @@ def measure_pft_batch(pft, torch, dev, stream, flush, frames: int = 4096, n: int
                         "adjoint_ms": ad, "adjoint_gbs": byts / ad / 1e6, "adjoint_frac": byts / ad / 1e6 / peak,
                         "fft_crop_ms": fc, "fft_crop_gbs": byts / fc / 1e6, "pft_speedup_vs_fft_crop": fc / f,
                         "frames_per_s_forward": frames / (f / 1e3)}
-        if M == 32:
-            out["M32"]["split_bf16"] = measure_split_bf16(pft, torch, plan, x, y, timed, byts, peak, kind, f, ad, fc)
+        out[f"M{M}"]["split_bf16"] = measure_split_bf16(pft, torch, plan, x, y, timed, byts, peak, kind, f, ad, fc,
+                                                        with_adjoint=(M == 32))
         del y, xa, plan
     del x
     torch.cuda.empty_cache()
@@ -469,23 +469,26 @@ def _csrc_sha(name: str) -> str:
 
 
 def _traffic(kernel: str, frames: int):
-    rec = TC_TRAFFIC[kernel]
+    rec = TC_TRAFFIC.get(kernel)
+    if rec is None:
+        return None
     if rec["bytes_per_frame"] and rec["source_sha256"] == _csrc_sha(rec["source"]):
         return rec["bytes_per_frame"] * frames
     return None
 
 
 def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32_fwd_ms, fp32_adj_ms,
-                       fft_crop_ms) -> dict:
-    """The split-BF16 tensor-core forward and adjoint (tcgen05) on the same
-    frames: times, HBM rooflines against the measured copy bandwidth, and the
-    largest per-frame relative difference from the FP32 CUDA-core PFT."""
+                       fft_crop_ms, with_adjoint: bool = True) -> dict:
+    """The split-BF16 tensor-core forward (and, for M = 32, adjoint) on the
+    same frames: times, HBM rooflines against the measured copy bandwidth, and
+    the largest per-frame relative difference from the FP32 CUDA-core PFT."""
     frames = x.shape[0]
-    tc = pft.Plan(x.shape[-1], 32, precision=pft.PREC_SPLIT_BF16)
+    M = y32.shape[-1]
+    tc = pft.Plan(x.shape[-1], M, precision=pft.PREC_SPLIT_BF16)
     y = torch.empty_like(y32)
     xa = torch.empty_like(x)
     f_ms = timed(lambda: tc.forward(x, out=y))
-    a_ms = timed(lambda: tc.adjoint(y, out=xa))
+    a_ms = timed(lambda: tc.adjoint(y, out=xa)) if with_adjoint else None
 
     def rel(a, b):
         d = torch.linalg.vector_norm((a - b).reshape(frames, -1), dim=1)
@@ -494,11 +497,14 @@ def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32
     plan32.forward(x, out=y32)
     torch.cuda.synchronize()
     rel_f = rel(y, y32)
-    x32 = plan32.adjoint(y32)
-    tc.adjoint(y32, out=xa)
-    torch.cuda.synchronize()
-    rel_a = rel(xa, x32)
-    del x32, xa, y, tc
+    rel_a = None
+    if with_adjoint:
+        x32 = plan32.adjoint(y32)
+        tc.adjoint(y32, out=xa)
+        torch.cuda.synchronize()
+        rel_a = rel(xa, x32)
+        del x32
+    del xa, y, tc
 
     def roof(kernel, ms):
         achieved = byts / ms / 1e6
@@ -506,12 +512,14 @@ def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32
                 "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes": byts,
                 "traffic": _traffic(kernel, frames)}
 
+    kf = "k_pft_tc_fwd" if M == 32 else "k_pft_tc64_fwd"
     return {"forward_ms": f_ms, "forward_gbs": byts / f_ms / 1e6, "frames_per_s_forward": frames / (f_ms / 1e3),
-            "adjoint_ms": a_ms, "adjoint_gbs": byts / a_ms / 1e6,
-            "speedup_vs_fp32": {"forward": fp32_fwd_ms / f_ms, "adjoint": fp32_adj_ms / a_ms},
+            "adjoint_ms": a_ms, "adjoint_gbs": byts / a_ms / 1e6 if a_ms else None,
+            "speedup_vs_fp32": {"forward": fp32_fwd_ms / f_ms, "adjoint": fp32_adj_ms / a_ms if a_ms else None},
             "speedup_vs_fft_crop": fft_crop_ms / f_ms,
             "max_rel_diff_vs_fp32": {"forward": rel_f, "adjoint": rel_a},
-            "roofline": {"forward": roof("k_pft_tc_fwd", f_ms), "adjoint": roof("k_pft_tc_adj", a_ms)}}
+            "roofline": {"forward": roof(kf, f_ms), "adjoint": roof("k_pft_tc_adj", a_ms) if a_ms else None},
+            "adjoint_note": None if with_adjoint else "split-BF16 adjoint built for M = 32 only"}
 
 
 def measure_pft_large(pft, torch, dev, stream, flush, cases=((8192, 4), (16384, 1)), reps: int = 5) -> dict:

@@ -416,7 +416,7 @@ __global__ void k_tc_table(int p, int q, int r, const double* __restrict__ a, ui
 
 namespace pfth {
 
-bool tc_supported(int n, int M, int p) { return n == kN && M == kM && p == kM / 2; }
+bool tc_supported(int n, int M, int p) { return n == kN && (M == kM || M == 2 * kM) && p == M / 2; }
 
 int tc_build_tables(pft_plan* plan) {
   double xi = 0.0, a[pftc::kMaxTerms] = {0};

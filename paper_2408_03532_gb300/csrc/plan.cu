@@ -364,10 +364,11 @@ int pft_plan_create(pft_plan** out, int n1, int n2, int M1, int M2, int p1, int 
   if (precision == PFT_PREC_SPLIT_BF16) {
     if (!pfth::tc_supported(p->n1, p->M1, p->p1)) {
       pft_plan_destroy(p);
-      return pfth::set_error(PFT_ERR_UNSUPPORTED, "split-BF16 is built for n=256, M=32, p=16 (got n=%d M=%d p=%d)",
-                             n1, M1, p1 ? p1 : M1 / 2);
+      return pfth::set_error(PFT_ERR_UNSUPPORTED,
+                             "split-BF16 is built for n=256 with M=32 (p=16) or M=64 (p=32), and for large frames "
+                             "(got n=%d M=%d p=%d)", n1, M1, p1 ? p1 : M1 / 2);
     }
-    rc = pfth::tc_build_tables(p);
+    rc = p->M1 == 64 ? pfth::tc64_build_tables(p) : pfth::tc_build_tables(p);
     if (rc != PFT_OK) {
       pft_plan_destroy(p);
       return rc;
@@ -428,6 +429,7 @@ int pft_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, voi
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
       return pfth::set_error(PFT_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
     if (plan->lf) return pfth::lf_forward(plan, x, y, batch, stream);
+    if (plan->M1 == 64) return pfth::tc64_forward(plan, x, y, batch, stream);
     return pfth::tc_forward(plan, x, y, batch, stream);
   }
   return launch_frames(plan, x, y, batch, stream, false);
@@ -441,6 +443,9 @@ int pft_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, voi
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
       return pfth::set_error(PFT_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
     if (plan->lf) return pfth::lf_adjoint(plan, y, x, batch, stream);
+    if (plan->M1 == 64)
+      return pfth::set_error(PFT_ERR_UNSUPPORTED, "the split-BF16 adjoint of n=256 frames is built for M=32; "
+                             "use a PFT_PREC_FP32 plan for M=64");
     return pfth::tc_adjoint(plan, y, x, batch, stream);
   }
   return launch_frames(plan, y, x, batch, stream, true);

@@ -138,9 +138,38 @@ def test_adjoint_matches_fp32_path_at_full_size(env, oracle_plans):
         assert rel_frames(x_tc[f].cpu().numpy()[None], ref)[0] < TOL
 
 
+@pytest.mark.parametrize("batch", [1, 2, 3, 5])
+def test_forward_m64_matches_oracle(env, batch):
+    """M = 64 (p = 32): the kernel stores rows t >= 0 and t = -32 of the
+    operator and forms Y[-t] from conj(A[t]); groups of 2 frames, ragged."""
+    torch, pft = env
+    x = synth.random_frames(batch, N, seed=80 + batch)
+    plan = pft.Plan(N, 64, precision=pft.PREC_SPLIT_BF16)
+    assert plan.info["p1"] == 32
+    y = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = opft.pft2(x.astype(np.complex128), *coeffs.plan_2d(N, N, 64, 64, 32, 32))
+    err = rel_frames(y, ref)
+    assert err.max() < TOL, err
+
+
+def test_forward_m64_full_size_and_adjoint_refused(env):
+    torch, pft = env
+    B = 4096
+    x = torch.randn(B, N, N, dtype=torch.complex64, device="cuda", generator=torch.Generator("cuda").manual_seed(4))
+    tc = pft.Plan(N, 64, precision=pft.PREC_SPLIT_BF16)
+    y_tc = tc.forward(x)
+    y_32 = pft.Plan(N, 64).forward(x)
+    torch.cuda.synchronize()
+    d = torch.linalg.vector_norm((y_tc - y_32).reshape(B, -1), dim=1) / torch.linalg.vector_norm(y_32.reshape(B, -1), dim=1)
+    assert float(d.max()) < 2 * TOL
+    with pytest.raises(pft.PftError) as e:
+        tc.adjoint(y_tc[:1])
+    assert e.value.code == -2
+
+
 def test_unsupported_shapes_and_empty(env):
     torch, pft = env
-    for n, m in [(128, 32), (256, 64), (64, 32)]:
+    for n, m in [(128, 32), (256, 16), (64, 32)]:
         with pytest.raises(pft.PftError) as e:
             pft.Plan(n, m, precision=pft.PREC_SPLIT_BF16)
         assert e.value.code == -2
