@@ -241,6 +241,8 @@ def main() -> None:
                     help="use the built-in cluster-size heuristic instead of timing each size (for profilers, "
                          "whose per-launch overhead distorts the autotuner's timings)")
     ap.add_argument("--no-pft-large", action="store_true")
+    ap.add_argument("--pft-large-cases", default="8192:4,16384:1",
+                    help="large-frame cases as n:frames[,n:frames...]")
     ap.add_argument("--only-pft-large", action="store_true",
                     help="run only the large-frame transforms and print their JSON (profiling target)")
     ap.add_argument("--only-pft-batch", action="store_true",
@@ -268,7 +270,8 @@ def main() -> None:
 
     if args.only_pft_large:
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-        print(json.dumps(measure_pft_large(pft, torch, dev, torch.cuda.current_stream(dev), flush)))
+        print(json.dumps(measure_pft_large(pft, torch, dev, torch.cuda.current_stream(dev), flush,
+                                           _cases(args.pft_large_cases))))
         return
     if args.only_pft_batch:
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -361,7 +364,8 @@ def main() -> None:
 
     pft_batch = None if args.no_pft_batch else measure_pft_batch(pft, torch, dev, stream, flush, args.pft_frames)
     batch64 = None if args.no_batch64 else measure_batch64(pft, synth, torch, dev, stream, flush)
-    pft_large = None if args.no_pft_large else measure_pft_large(pft, torch, dev, stream, flush)
+    pft_large = None if args.no_pft_large else measure_pft_large(pft, torch, dev, stream, flush,
+                                                                 _cases(args.pft_large_cases))
 
     # roofline of the dominant kernel (per sweep of launches of that kernel)
     pinfo = pft.Plan(n, M).info
@@ -454,13 +458,17 @@ def measure_pft_batch(pft, torch, dev, stream, flush, frames: int = 4096, n: int
 # DRAM traffic (read + write bytes per frame) of the split-BF16 kernels from
 # ncu captures, each valid only for the source file it was taken on.
 TC_TRAFFIC = {
-    # 4096 frames of 256 x 256, M = 32; median of 6 / 7 launches (one ncu pass each)
-    "k_pft_tc_fwd": {"source": "pft_tc.cu", "source_sha256": "e013619d75cb25739010e0d00ea07d0c9d34d37060fc6ac0de7378992fd6419a",
-                     "bytes_per_frame": (2147638016 + 30002432) / 4096},
-    "k_pft_tc_adj": {"source": "pft_tc_adj.cu", "source_sha256": "e3d99338b748ea0a4d4b0ce7b38083d91766084346370a63963eba7c5346de3e",
-                     "bytes_per_frame": (33714944 + 2082775552) / 4096},
+    # 4096 frames of 256 x 256; median of 6 / 7 launches (one ncu pass each)
+    "k_pft_tc_fwd": {"source": "pft_tc.cu",
+                     "source_sha256": "839c18933284936e893370a5a37f2862a4b921ff5d9d6c453388e3c9d9ad2f99",
+                     "bytes_per_frame": (2147667200 + 29974144) / 4096},
+    "k_pft_tc_adj": {"source": "pft_tc_adj.cu",
+                     "source_sha256": "e3d99338b748ea0a4d4b0ce7b38083d91766084346370a63963eba7c5346de3e",
+                     "bytes_per_frame": (33727488 + 2082485248) / 4096},
+    "k_pft_tc64_fwd": {"source": "pft_tc64.cu",
+                       "source_sha256": "51d1063f28e7b2d2262b923d7d15487f49b5e31601997292cad3b4d2e53ec0b6",
+                       "bytes_per_frame": (2149727872 + 122555776) / 4096},
 }
-
 
 def _csrc_sha(name: str) -> str:
     import hashlib
@@ -520,6 +528,10 @@ def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32
             "max_rel_diff_vs_fp32": {"forward": rel_f, "adjoint": rel_a},
             "roofline": {"forward": roof(kf, f_ms), "adjoint": roof("k_pft_tc_adj", a_ms) if a_ms else None},
             "adjoint_note": None if with_adjoint else "split-BF16 adjoint built for M = 32 only"}
+
+
+def _cases(spec: str) -> tuple:
+    return tuple(tuple(int(v) for v in c.split(":")) for c in spec.split(",") if c)
 
 
 def measure_pft_large(pft, torch, dev, stream, flush, cases=((8192, 4), (16384, 1)), reps: int = 5) -> dict:
