@@ -104,6 +104,25 @@ int pft_choose_r(double eps, double ratio, int* r);
  *   choice, else forced; path: PFT_PATH_*; precision: PFT_PREC_*.
  *   Synchronises the device once (table generation). UNSUPPORTED when the
  *   sizes are outside the built kernels (the message says which).
+ * Built shapes (square frames, p = M/2):
+ *   PFT_PREC_FP32        (n, M) in {(32, 16), (64, 16), (64, 32), (64, 64),
+ *                        (128, 16), (128, 32), (128, 64), (256, 16),
+ *                        (256, 32), (256, 64)} (forward and adjoint, CUDA
+ *                        cores);
+ *   PFT_PREC_SPLIT_BF16  n = 256 with M = 32 (forward and adjoint) or
+ *                        M = 64 (forward; the adjoint returns UNSUPPORTED),
+ *                        tensor cores with the per-axis operator folded
+ *                        into one table;
+ *                        n in {2048, 4096, 8192, 16384} with M = 128
+ *                        (p = 64, q = n / 64; forward and adjoint): the
+ *                        paper's large-frame regime, stage A of Algorithm 5
+ *                        on tensor cores, stage B on CUDA cores; frames go in
+ *                        passes through a plan-owned workspace of <= 32 MB.
+ *   A split-BF16 plan's results carry a relative error of about 1e-5 per
+ *   frame (BF16 hi + lo operands, three partial products per term).
+ *   Device-side waits of the tensor-core kernels are bounded (2 s); a timeout
+ *   is latched in the plan and returned as PFT_ERR_TIMEOUT by its next
+ *   pft_forward / pft_adjoint call.
  */
 typedef struct pft_plan pft_plan;
 
