@@ -447,8 +447,7 @@ def measure_pft_batch(pft, torch, dev, stream, flush, frames: int = 4096, n: int
                         "adjoint_ms": ad, "adjoint_gbs": byts / ad / 1e6, "adjoint_frac": byts / ad / 1e6 / peak,
                         "fft_crop_ms": fc, "fft_crop_gbs": byts / fc / 1e6, "pft_speedup_vs_fft_crop": fc / f,
                         "frames_per_s_forward": frames / (f / 1e3)}
-        out[f"M{M}"]["split_bf16"] = measure_split_bf16(pft, torch, plan, x, y, timed, byts, peak, kind, f, ad, fc,
-                                                        with_adjoint=(M == 32))
+        out[f"M{M}"]["split_bf16"] = measure_split_bf16(pft, torch, plan, x, y, timed, byts, peak, kind, f, ad, fc)
         del y, xa, plan
     del x
     torch.cuda.empty_cache()
@@ -487,9 +486,9 @@ def _traffic(kernel: str, frames: int):
 
 def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32_fwd_ms, fp32_adj_ms,
                        fft_crop_ms, with_adjoint: bool = True) -> dict:
-    """The split-BF16 tensor-core forward (and, for M = 32, adjoint) on the
-    same frames: times, HBM rooflines against the measured copy bandwidth, and
-    the largest per-frame relative difference from the FP32 CUDA-core PFT."""
+    """The split-BF16 tensor-core forward and adjoint on the same frames: times,
+    HBM rooflines against the measured copy bandwidth, and the largest
+    per-frame relative difference from the FP32 CUDA-core PFT."""
     frames = x.shape[0]
     M = y32.shape[-1]
     tc = pft.Plan(x.shape[-1], M, precision=pft.PREC_SPLIT_BF16)
@@ -520,14 +519,13 @@ def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32
                 "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes": byts,
                 "traffic": _traffic(kernel, frames)}
 
-    kf = "k_pft_tc_fwd" if M == 32 else "k_pft_tc64_fwd"
+    kf, ka = ("k_pft_tc_fwd", "k_pft_tc_adj") if M == 32 else ("k_pft_tc64_fwd", "k_pft_tc64_adj")
     return {"forward_ms": f_ms, "forward_gbs": byts / f_ms / 1e6, "frames_per_s_forward": frames / (f_ms / 1e3),
             "adjoint_ms": a_ms, "adjoint_gbs": byts / a_ms / 1e6 if a_ms else None,
             "speedup_vs_fp32": {"forward": fp32_fwd_ms / f_ms, "adjoint": fp32_adj_ms / a_ms if a_ms else None},
             "speedup_vs_fft_crop": fft_crop_ms / f_ms,
             "max_rel_diff_vs_fp32": {"forward": rel_f, "adjoint": rel_a},
-            "roofline": {"forward": roof(kf, f_ms), "adjoint": roof("k_pft_tc_adj", a_ms) if a_ms else None},
-            "adjoint_note": None if with_adjoint else "split-BF16 adjoint built for M = 32 only"}
+            "roofline": {"forward": roof(kf, f_ms), "adjoint": roof(ka, a_ms) if a_ms else None}}
 
 
 def _cases(spec: str) -> tuple:

@@ -369,6 +369,7 @@ int pft_plan_create(pft_plan** out, int n1, int n2, int M1, int M2, int p1, int 
                              "(got n=%d M=%d p=%d)", n1, M1, p1 ? p1 : M1 / 2);
     }
     rc = p->M1 == 64 ? pfth::tc64_build_tables(p) : pfth::tc_build_tables(p);
+    if (rc == PFT_OK && p->M1 == 64) rc = pfth::tc64_build_adjoint_table(p);
     if (rc != PFT_OK) {
       pft_plan_destroy(p);
       return rc;
@@ -443,9 +444,7 @@ int pft_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, voi
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
       return pfth::set_error(PFT_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
     if (plan->lf) return pfth::lf_adjoint(plan, y, x, batch, stream);
-    if (plan->M1 == 64)
-      return pfth::set_error(PFT_ERR_UNSUPPORTED, "the split-BF16 adjoint of n=256 frames is built for M=32; "
-                             "use a PFT_PREC_FP32 plan for M=64");
+    if (plan->M1 == 64) return pfth::tc64_adjoint(plan, y, x, batch, stream);
     return pfth::tc_adjoint(plan, y, x, batch, stream);
   }
   return launch_frames(plan, y, x, batch, stream, true);

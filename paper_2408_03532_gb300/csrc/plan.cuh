@@ -44,6 +44,8 @@ int tc_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void
 int tc_build_adjoint_table(pft_plan* plan, const double* d_a);
 int tc64_build_tables(pft_plan* plan);
 int tc64_forward(const pft_plan* plan, const void* x, void* y, int64_t batch, void* stream);
+int tc64_build_adjoint_table(pft_plan* plan);
+int tc64_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void* stream);
 int tc_adjoint(const pft_plan* plan, const void* y, void* x, int64_t batch, void* stream);
 
 // Large frames, n in {2048, 4096, 8192} with M = 128 (pft_lf.cu).

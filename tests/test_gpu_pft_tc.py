@@ -1,5 +1,5 @@
 """GPU parity of the split-BF16 tensor-core PFT and its adjoint (256 x 256
-frames, M = 32) against the FP64 oracle.
+frames, M = 32 and M = 64) against the FP64 oracle.
 
 Tolerance: every operand is split into BF16 hi + lo (|v - hi - lo| <= 2^-17 |v|)
 and each product is formed from three partial products, so a product carries
@@ -152,19 +152,74 @@ def test_forward_m64_matches_oracle(env, batch):
     assert err.max() < TOL, err
 
 
-def test_forward_m64_full_size_and_adjoint_refused(env):
+def test_forward_m64_full_size(env):
     torch, pft = env
     B = 4096
     x = torch.randn(B, N, N, dtype=torch.complex64, device="cuda", generator=torch.Generator("cuda").manual_seed(4))
-    tc = pft.Plan(N, 64, precision=pft.PREC_SPLIT_BF16)
-    y_tc = tc.forward(x)
+    y_tc = pft.Plan(N, 64, precision=pft.PREC_SPLIT_BF16).forward(x)
     y_32 = pft.Plan(N, 64).forward(x)
     torch.cuda.synchronize()
     d = torch.linalg.vector_norm((y_tc - y_32).reshape(B, -1), dim=1) / torch.linalg.vector_norm(y_32.reshape(B, -1), dim=1)
     assert float(d.max()) < 2 * TOL
-    with pytest.raises(pft.PftError) as e:
-        tc.adjoint(y_tc[:1])
-    assert e.value.code == -2
+
+
+@pytest.mark.parametrize("batch", [1, 2, 3, 5, 153])
+def test_adjoint_m64_matches_oracle(env, batch):
+    """M = 64 adjoint: the kernel folds Y along each axis (u = y[s] + y[-s],
+    w = -i (y[s] - y[-s])) and applies a real table; 153 frames put two frames
+    on one SM."""
+    torch, pft = env
+    yv = synth.random_frames(batch, 64, seed=90 + batch)
+    plan = pft.Plan(N, 64, precision=pft.PREC_SPLIT_BF16)
+    x = plan.adjoint(torch.from_numpy(yv).cuda()).cpu().numpy()
+    ref = opft.pft2_adjoint(yv.astype(np.complex128), *coeffs.plan_2d(N, N, 64, 64, 32, 32))
+    err = rel_frames(x, ref)
+    assert err.max() < TOL, err
+
+
+def test_adjoint_m64_fold_edges(env):
+    """Inputs that live only on the rows / columns the fold treats apart:
+    t = 0 (no partner), t = -32 (no partner), a single pair (s, -s), and a
+    zero frame."""
+    torch, pft = env
+    yv = np.zeros((7, 64, 64), np.complex64)
+    yv[0, 32, :] = synth.random_frames(1, 64, seed=1)[0, 0]     # t1 = 0
+    yv[1, :, 32] = synth.random_frames(1, 64, seed=2)[0, 0]     # t2 = 0
+    yv[2, 0, :] = synth.random_frames(1, 64, seed=3)[0, 0]      # t1 = -32
+    yv[3, :, 0] = synth.random_frames(1, 64, seed=4)[0, 0]      # t2 = -32
+    yv[4, 0, 0] = 1 - 2j                                        # (-32, -32)
+    yv[5, 32 + 5, 32 - 7] = 0.5 + 1j                            # (5, -7)
+    yv[5, 32 - 5, 32 + 7] = -2 + 0.25j                          # (-5, 7)
+    plan = pft.Plan(N, 64, precision=pft.PREC_SPLIT_BF16)
+    x = plan.adjoint(torch.from_numpy(yv).cuda()).cpu().numpy()
+    ref = opft.pft2_adjoint(yv[:6].astype(np.complex128), *coeffs.plan_2d(N, N, 64, 64, 32, 32))
+    err = rel_frames(x[:6], ref)
+    assert err.max() < TOL, err
+    assert np.all(x[6] == 0)
+
+
+def test_adjoint_m64_identity_and_full_size(env):
+    """<A x, y> = <x, A^H y> for the M = 64 split pair, and 4096 frames against
+    the FP32 CUDA-core adjoint."""
+    torch, pft = env
+    plan = pft.Plan(N, 64, precision=pft.PREC_SPLIT_BF16)
+    x = synth.random_frames(4, N, seed=31)
+    yv = synth.random_frames(4, 64, seed=32)
+    Ax = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.complex128)
+    Ahy = plan.adjoint(torch.from_numpy(yv).cuda()).cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(yv.astype(np.complex128), Ax)
+    rhs = np.vdot(Ahy, x.astype(np.complex128))
+    assert abs(lhs - rhs) <= 2 * TOL * np.linalg.norm(Ax) * np.linalg.norm(yv)
+    B = 4096
+    yb = torch.randn(B, 64, 64, dtype=torch.complex64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    x_tc = plan.adjoint(yb)
+    x_32 = pft.Plan(N, 64).adjoint(yb)
+    torch.cuda.synchronize()
+    d = torch.linalg.vector_norm((x_tc - x_32).reshape(B, -1), dim=1) / torch.linalg.vector_norm(x_32.reshape(B, -1), dim=1)
+    assert float(d.max()) < 2 * TOL
+    for f in (0, 151, 152, 4095):
+        ref = opft.pft2_adjoint(yb[f].cpu().numpy().astype(np.complex128)[None], *coeffs.plan_2d(N, N, 64, 64, 32, 32))
+        assert rel_frames(x_tc[f].cpu().numpy()[None], ref)[0] < TOL
 
 
 def test_unsupported_shapes_and_empty(env):
@@ -177,3 +232,5 @@ def test_unsupported_shapes_and_empty(env):
     empty = torch.empty(0, N, N, dtype=torch.complex64, device="cuda")
     assert plan.forward(empty).shape == (0, M, M)
     assert plan.adjoint(torch.empty(0, M, M, dtype=torch.complex64, device="cuda")).shape == (0, N, N)
+    plan64 = pft.Plan(N, 64, precision=pft.PREC_SPLIT_BF16)
+    assert plan64.adjoint(torch.empty(0, 64, 64, dtype=torch.complex64, device="cuda")).shape == (0, N, N)
