@@ -101,16 +101,14 @@ __device__ __forceinline__ void split_store(uint8_t* base, uint32_t comp_bytes, 
   *reinterpret_cast<__nv_bfloat162*>(base + comp_bytes + off) = lo;
 }
 
-// Splits v into BF16 hi + lo; the lane pair (2r, 2r+1) exchanges its parts so
-// that the even lane writes (hi_2r, hi_2r+1) and the odd lane (lo_2r, lo_2r+1)
-// at `off` (the odd lane's `off` already points into the lo component).
-__device__ __forceinline__ void pair_store(uint8_t* base, uint32_t off, float v, bool odd) {
+// Each lane stores its own BF16 hi and lo parts (2-byte stores): lanes are
+// K-adjacent rows, so a warp fills whole 16-byte core-matrix rows without any
+// lane exchange.
+__device__ __forceinline__ void own_store(uint8_t* base, uint32_t off, uint32_t lo_off, float v) {
   const __nv_bfloat16 hi = __float2bfloat16_rn(v);
   const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-  const uint32_t mine = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
-  const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
-  const uint32_t word = odd ? ((other >> 16) | (mine & 0xFFFF0000u)) : ((mine & 0xFFFFu) | (other << 16));
-  *reinterpret_cast<uint32_t*>(base + off) = word;
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = hi;
+  *reinterpret_cast<__nv_bfloat16*>(base + lo_off + off) = lo;
 }
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
@@ -246,10 +244,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     // ------------------------------------------------------------- epilogue
     const int q = warp;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    // Lanes 2r and 2r+1 hold K-adjacent rows: the even lane stores both hi
-    // parts, the odd lane both lo parts, as one 32-bit word each.
-    const bool odd = lane & 1;
-    const uint32_t kofs = (uint32_t)(lane >> 3) * A2_LBO + (uint32_t)((lane & 7) >> 1) * 4 + (odd ? A2_COMP : 0u);
+    const uint32_t kofs = (uint32_t)(lane >> 3) * A2_LBO + (uint32_t)(lane & 7) * 2;
     long long T = 0;
     for (long long it = 0; it < nloc; ++it) {
       const long long g = blockIdx.x + it * gridDim.x;
@@ -273,7 +268,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               const uint32_t m2 = (uint32_t)(q * kM + 16 * h + t);
-              pair_store(a2, kofs + (m2 >> 3) * CM + (m2 & 7) * 16, p0[t] - p1[t], odd);
+              own_store(a2, kofs + (m2 >> 3) * CM + (m2 & 7) * 16, A2_COMP, p0[t] - p1[t]);
             }
             tmem_ld16(z1 + kM + 16 * h, p0);
             tmem_ld16(z2 + 16 * h, p1);
@@ -281,7 +276,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               const uint32_t m2 = (uint32_t)(q * kM + 16 * h + t);
-              pair_store(a2 + 2 * A2_COMP, kofs + (m2 >> 3) * CM + (m2 & 7) * 16, p0[t] + p1[t], odd);
+              own_store(a2 + 2 * A2_COMP, kofs + (m2 >> 3) * CM + (m2 & 7) * 16, A2_COMP, p0[t] + p1[t]);
             }
           }
         }

@@ -66,15 +66,14 @@ __device__ __forceinline__ void split_store(uint8_t* base, uint32_t comp_bytes, 
   *reinterpret_cast<__nv_bfloat162*>(base + comp_bytes + off) = lo;
 }
 
-// Lanes 2r, 2r + 1 hold K-adjacent rows: the even lane stores both hi parts,
-// the odd lane both lo parts (its `off` already points into the lo component).
-__device__ __forceinline__ void pair_store(uint8_t* base, uint32_t off, float v, bool odd) {
+// Each lane stores its own BF16 hi and lo parts (2-byte stores): lanes are
+// K-adjacent rows, so a warp fills whole 16-byte core-matrix rows without any
+// lane exchange.
+__device__ __forceinline__ void own_store(uint8_t* base, uint32_t off, uint32_t lo_off, float v) {
   const __nv_bfloat16 hi = __float2bfloat16_rn(v);
   const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-  const uint32_t mine = (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
-  const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
-  const uint32_t word = odd ? ((other >> 16) | (mine & 0xFFFF0000u)) : ((mine & 0xFFFFu) | (other << 16));
-  *reinterpret_cast<uint32_t*>(base + off) = word;
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = hi;
+  *reinterpret_cast<__nv_bfloat16*>(base + lo_off + off) = lo;
 }
 
 // Reads Z1[s], Z1[33 + s], Z2[s], Z2[33 + s] for s = s0 .. s0 + 15 (s0 < 32)
@@ -221,8 +220,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // TMEM lane 32 q + lane = (frame q >> 1, row 32 (q & 1) + lane of the tile)
     const int q = warp, h = q & 1;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const bool odd = lane & 1;
-    const uint32_t kofs = (uint32_t)(lane >> 3) * A2_LBO + (uint32_t)((lane & 7) >> 1) * 4 + (odd ? A2_COMP : 0u);
+    const uint32_t kofs = (uint32_t)(lane >> 3) * A2_LBO + (uint32_t)(lane & 7) * 2;
     long long T = 0;
     for (long long it = 0; it < nloc; ++it) {
       const long long g = blockIdx.x + it * gridDim.x;
@@ -237,8 +235,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           recombine(tmem + lane_off + b * ACC_COLS, [&](int ti, float re, float im) {
             const uint32_t m2 = fbase + (uint32_t)ti;
             const uint32_t off = kofs + (m2 >> 3) * CM + (m2 & 7) * 16;
-            pair_store(a2, off, re, odd);
-            pair_store(a2 + 2 * A2_COMP, off, im, odd);
+            own_store(a2, off, A2_COMP, re);
+            own_store(a2 + 2 * A2_COMP, off, A2_COMP, im);
           });
         }
         tc_fence_before();
