@@ -459,14 +459,17 @@ def measure_pft_batch(pft, torch, dev, stream, flush, frames: int = 4096, n: int
 TC_TRAFFIC = {
     # 4096 frames of 256 x 256; median of 6 / 7 launches (one ncu pass each)
     "k_pft_tc_fwd": {"source": "pft_tc.cu",
-                     "source_sha256": "839c18933284936e893370a5a37f2862a4b921ff5d9d6c453388e3c9d9ad2f99",
-                     "bytes_per_frame": (2147667200 + 29974144) / 4096},
+                     "source_sha256": "e9cda75fbc3b27ecc1405097e3681af2dc09b650905fd4ee4102100457d2df1d",
+                     "bytes_per_frame": (2147662336 + 29972608) / 4096},
     "k_pft_tc_adj": {"source": "pft_tc_adj.cu",
                      "source_sha256": "e3d99338b748ea0a4d4b0ce7b38083d91766084346370a63963eba7c5346de3e",
-                     "bytes_per_frame": (33727488 + 2082485248) / 4096},
+                     "bytes_per_frame": (33716480 + 2082690560) / 4096},
     "k_pft_tc64_fwd": {"source": "pft_tc64.cu",
-                       "source_sha256": "51d1063f28e7b2d2262b923d7d15487f49b5e31601997292cad3b4d2e53ec0b6",
-                       "bytes_per_frame": (2149727872 + 122555776) / 4096},
+                       "source_sha256": "5fcaf83cb9ebd00ada031dd48effd9652351ff3f29e1b6f6e2eee59c7651baaf",
+                       "bytes_per_frame": (2149662464 + 124201856) / 4096},
+    "k_pft_tc64_adj": {"source": "pft_tc64_adj.cu",
+                       "source_sha256": "d9af80253fb834e09a235ebe347ee3689edac01c8f29a5eab02ad3454ddbb784",
+                       "bytes_per_frame": (134392576 + 2082455296) / 4096},
 }
 
 def _csrc_sha(name: str) -> str:
