@@ -109,10 +109,10 @@ int pft_choose_r(double eps, double ratio, int* r);
  *                        (128, 16), (128, 32), (128, 64), (256, 16),
  *                        (256, 32), (256, 64)} (forward and adjoint, CUDA
  *                        cores);
- *   PFT_PREC_SPLIT_BF16  n = 256 with M = 32 (forward and adjoint) or
- *                        M = 64 (forward; the adjoint returns UNSUPPORTED),
- *                        tensor cores with the per-axis operator folded
- *                        into one table;
+ *   PFT_PREC_SPLIT_BF16  n = 256 with M = 32 or M = 64 (forward and
+ *                        adjoint), tensor cores with the per-axis operator
+ *                        folded into one table (at M = 64 only the rows
+ *                        t >= 0 and t = -M/2, using A[-t] = conj(A[t]));
  *                        n in {2048, 4096, 8192, 16384} with M = 128
  *                        (p = 64, q = n / 64; forward and adjoint): the
  *                        paper's large-frame regime, stage A of Algorithm 5
