@@ -82,6 +82,15 @@ struct Cluster {
   }
 };
 
+// 4-byte asynchronous global -> shared copies (the amplitudes of a position
+// are fetched while the transforms run).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Modulus-projection residual (Eq. 3) and its contribution to the objective.
 template <int MODE>
 __device__ __forceinline__ float2 residual(float2 Psi, float d, double& acc) {
@@ -172,6 +181,22 @@ __device__ __forceinline__ void apply_update(const PieArgs& a, const PieItem& p,
   }
 }
 
+// The same with the object value at oidx already in a register (read when the
+// position started: no other work item writes the patch meanwhile).
+template <int MODE>
+__device__ __forceinline__ void apply_update_at(const PieArgs& a, const PieItem& p, long long oidx, float2 w,
+                                                float2 zold, float2 dpsi, int pidx) {
+  if (MODE == MODE_COLOURED) {
+    const float2 u = cmulc(dpsi, w);  // conj(w) dpsi
+    p.obj[oidx] = make_float2(fmaf(-p.coef, u.x, zold.x), fmaf(-p.coef, u.y, zold.y));
+  } else if (MODE == MODE_BATCHED) {
+    atomicAdd(p.acc + oidx, cscale(cmulc(dpsi, w), p.coef));
+  } else {
+    atomicAdd(p.acc + oidx, cmulc(dpsi, w));
+    if (a.gprobe) atomicAdd(a.gprobe + pidx, cmulc(dpsi, zold));
+  }
+}
+
 // Blind PIE, second round: accumulate conj(z_new) dpsi' and |z_new|^2 per probe pixel.
 __device__ __forceinline__ void accumulate_probe(const PieArgs& a, const PieItem& p, long long oidx, float2 dpsi,
                                                  int pidx, float inv_n2) {
@@ -208,7 +233,8 @@ struct PiePftShape {
   static constexpr int OFF_G = (C == 1) ? OFF_Y : OFF_Y + Y_SIZE;  // alias for one CTA
   static constexpr int OFF_Z = (C == 1) ? OFF_Y + (Y_SIZE > G_SIZE ? Y_SIZE : G_SIZE) : OFF_G + G_SIZE;
   static constexpr int OFF_RED = OFF_Z + M * ZS;
-  static constexpr size_t SMEM = sizeof(float2) * (OFF_RED + 16);
+  static constexpr int OFF_D = OFF_RED + 16;           // amplitudes of the CTA's columns: [M][CM] floats
+  static constexpr size_t SMEM = sizeof(float2) * (OFF_D + (M * CM + 1) / 2);
 };
 
 template <int P, int Q, int MP, int MODE, int C, int NT>
@@ -226,20 +252,42 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
   float2* sG = sm + S::OFF_G;
   float2* sZ = sm + S::OFF_Z;
   double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
-  for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) sm[i] = gW[i];
-  fill_stage_table<P>(stw, gtw, P);
+  float* sD = reinterpret_cast<float*>(sm + S::OFF_D);
   const unsigned rank = CL::rank();
-  CL::sync();  // every CTA of the cluster has started before any remote store
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = lane % P, g = lane / P;
   const int r0 = rank * RN;
+  // With one row group per warp, the probe and patch values of the warp's rows
+  // stay in registers from the exit wave to the update, and the next work
+  // item's are loaded as soon as the current one is done.
+  constexpr bool KEEP = (RN == NW * G);
+  float2 wv[Q], zv[Q];
+  auto gather = [&](const PieItem& q) {
+    for (int i = threadIdx.x; i < M * CM; i += NT) cp_async4(sD + i, q.dat + rank * CM + (i / CM) * M + (i % CM));
+    if constexpr (KEEP) {
+      const int u = r0 + warp * G + g;
+#pragma unroll
+      for (int l = 0; l < Q; ++l) {
+        const int v = Q * k + l;
+        wv[l] = __ldg(q.probe + u * N + v);
+        zv[l] = q.objr[q.obase + (long long)u * q.obj_w + v];
+      }
+    }
+  };
+  const int step = gridDim.x / C;
+  int it = blockIdx.x / C;
+  if (it < a.count) gather(resolve<M * M>(a, it));
+  for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) sm[i] = gW[i];
+  fill_stage_table<P>(stw, gtw, P);
+  CL::sync();  // every CTA of the cluster has started before any remote store
   LaneNet<P, false> net;
   net.init(k, stw);
   const int rounds = (MODE == MODE_COLOURED && a.pacc) ? 2 : 1;
-  for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
+  for (; it < a.count; it += step) {
     const PieItem p = resolve<M * M>(a, it);
     const long long obase = p.obase;
     for (int round = 0; round < rounds; ++round) {
+    if (KEEP && round == 1) gather(p);  // the updated patch
     // 1. rows (axis 2) of the exit wave -> column owners
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int u = r0 + u0 + g;
@@ -247,7 +295,10 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
         const int v = Q * k + l;
-        xv[l] = cmul(__ldg(p.probe + u * N + v), p.objr[obase + (long long)u * p.obj_w + v]);
+        if constexpr (KEEP)
+          xv[l] = cmul(wv[l], zv[l]);
+        else
+          xv[l] = cmul(__ldg(p.probe + u * N + v), p.objr[obase + (long long)u * p.obj_w + v]);
       }
       T::forward(xv, k, c.bh[1], sW2, net, [&](int t, float2 val) {
         float2* dst = CL::map(sY, (unsigned)(t / CM));
@@ -263,13 +314,13 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
       for (int l = 0; l < Q; ++l) xv[l] = sY[tl * S::SYT + Q * k + l + k];
       T::forward(xv, k, c.bh[0], sW1, net, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
     }
+    cp_async_wait_all();
     __syncthreads();
     // 3b. modulus projection on the M x CM coefficients
-    const float* dj = p.dat + rank * CM;
     double part = 0.0;
     for (int i = threadIdx.x; i < M * CM; i += NT) {
       float2* z = sZ + (i / CM) * S::ZS + (i % CM);
-      *z = residual<MODE>(*z, __ldg(dj + (i / CM) * M + (i % CM)), part);
+      *z = residual<MODE>(*z, sD[i], part);
     }
     block_accumulate<NT>(round == 0 ? part : 0.0, sred, p.red);
     __syncthreads();
@@ -294,14 +345,19 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
       for (int l = 0; l < Q; ++l) {
         const int v = Q * k + l;
         const long long oidx = obase + (long long)u * p.obj_w + v;
-        if (round == 0)
-          apply_update<MODE>(a, p, oidx, __ldg(p.probe + u * N + v), xv[l], u * N + v);
-        else
+        if (round == 0) {
+          if constexpr (KEEP)
+            apply_update_at<MODE>(a, p, oidx, wv[l], zv[l], xv[l], u * N + v);
+          else
+            apply_update<MODE>(a, p, oidx, __ldg(p.probe + u * N + v), xv[l], u * N + v);
+        } else {
           accumulate_probe(a, p, oidx, xv[l], u * N + v, 1.f / (float)(N * N));
+        }
       }
     }
     if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
     }  // round
+    if (it + step < a.count) gather(resolve<M * M>(a, it + step));
     if constexpr (C == 1) __syncthreads();
   }
 }
@@ -318,7 +374,8 @@ struct PieFullShape {
   static constexpr int OFF_C = F::TAB;
   static constexpr int OFF_R = (C == 1) ? OFF_C : OFF_C + N * SCS;  // alias for one CTA
   static constexpr int OFF_RED = (C == 1) ? OFF_C + N * SCS : OFF_R + RN * SRS;
-  static constexpr size_t SMEM = sizeof(float2) * (OFF_RED + 16);
+  static constexpr int OFF_D = OFF_RED + 16;  // amplitudes of the CTA's slot columns: [N][CN] floats
+  static constexpr size_t SMEM = sizeof(float2) * (OFF_D + (N * CN + 1) / 2);
 };
 
 template <int N, int MODE, int C, int NT>
@@ -332,19 +389,41 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
   float2* sC = sm + S::OFF_C;
   float2* sR = sm + S::OFF_R;
   double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
-  F::fill(tw, gtw);
+  float* sD = reinterpret_cast<float*>(sm + S::OFF_D);
   const unsigned rank = CL::rank();
-  CL::sync();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l = lane % L, g = lane / L;
   const int r0 = rank * RN, c0 = rank * CN;
+  // As in the PFT variant: with one row group per warp the probe and patch
+  // values stay in registers from the exit wave to the update.
+  constexpr bool KEEP = (RN == NW * G);
+  float2 wv[E], zv[E];
+  auto gather = [&](const PieItem& q) {
+    for (int i = threadIdx.x; i < N * CN; i += NT)
+      cp_async4(sD + i, q.dat + F::freq_of_slot(i / CN) * N + F::freq_of_slot(c0 + i % CN));
+    if constexpr (KEEP) {
+      const int u = r0 + warp * G + g;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = l + L * e;
+        wv[e] = __ldg(q.probe + u * N + v);
+        zv[e] = q.objr[q.obase + (long long)u * q.obj_w + v];
+      }
+    }
+  };
+  const int step = gridDim.x / C;
+  int it = blockIdx.x / C;
+  if (it < a.count) gather(resolve<N * N>(a, it));
+  F::fill(tw, gtw);
+  CL::sync();
   typename F::Net net;
   F::init_net(net, l, tw);
   const int rounds = (MODE == MODE_COLOURED && a.pacc) ? 2 : 1;
-  for (int it = blockIdx.x / C; it < a.count; it += gridDim.x / C) {
+  for (; it < a.count; it += step) {
     const PieItem p = resolve<N * N>(a, it);
     const long long obase = p.obase;
     for (int round = 0; round < rounds; ++round) {
+    if (KEEP && round == 1) gather(p);  // the updated patch
     // 1. FFT of this CTA's rows of the exit wave -> column-slot owners
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int u = r0 + u0 + g;
@@ -352,7 +431,10 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int v = l + L * e;
-        x[e] = cmul(__ldg(p.probe + u * N + v), p.objr[obase + (long long)u * p.obj_w + v]);
+        if constexpr (KEEP)
+          x[e] = cmul(wv[e], zv[e]);
+        else
+          x[e] = cmul(__ldg(p.probe + u * N + v), p.objr[obase + (long long)u * p.obj_w + v]);
       }
       F::fwd(x, l, tw, net);
 #pragma unroll
@@ -372,14 +454,13 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
 #pragma unroll
       for (int p = 0; p < E; ++p) sC[(p * L + l) * S::SCS + b] = x[p];
     }
+    cp_async_wait_all();
     __syncthreads();
     // 3b. modulus projection
-    const float* dj = p.dat;
     double part = 0.0;
     for (int i = threadIdx.x; i < N * CN; i += NT) {
-      const int sa = i / CN, sb = i % CN;
-      float2* z = sC + sa * S::SCS + sb;
-      *z = residual<MODE>(*z, __ldg(dj + F::freq_of_slot(sa) * N + F::freq_of_slot(c0 + sb)), part);
+      float2* z = sC + (i / CN) * S::SCS + (i % CN);
+      *z = residual<MODE>(*z, sD[i], part);
     }
     block_accumulate<NT>(round == 0 ? part : 0.0, sred, p.red);
     __syncthreads();
@@ -408,14 +489,19 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
       for (int e = 0; e < E; ++e) {
         const int v = l + L * e;
         const long long oidx = obase + (long long)u * p.obj_w + v;
-        if (round == 0)
-          apply_update<MODE>(a, p, oidx, __ldg(p.probe + u * N + v), x[e], u * N + v);
-        else
+        if (round == 0) {
+          if constexpr (KEEP)
+            apply_update_at<MODE>(a, p, oidx, wv[e], zv[e], x[e], u * N + v);
+          else
+            apply_update<MODE>(a, p, oidx, __ldg(p.probe + u * N + v), x[e], u * N + v);
+        } else {
           accumulate_probe(a, p, oidx, x[e], u * N + v, 1.f / (float)(N * N));
+        }
       }
     }
     if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
     }  // round
+    if (it + step < a.count) gather(resolve<N * N>(a, it + step));
     if constexpr (C == 1) __syncthreads();
   }
 }
