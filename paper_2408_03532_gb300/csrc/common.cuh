@@ -79,6 +79,35 @@ __device__ __forceinline__ void fill_stage_table(float2* tws, const float2* __re
   }
 }
 
+// Asynchronous global -> shared copies (cp.async, L1-allocating): the caller
+// commits the group and waits for it before the data are read.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// fill_stage_table through cp.async.
+template <int L>
+__device__ __forceinline__ void fill_stage_table_async(float2* tws, const float2* __restrict__ src, int NS) {
+  for (int i = threadIdx.x; i < L - 1; i += blockDim.x) {
+    int h = 1;
+    while (2 * h <= i + 1) h *= 2;
+    cp_async8(tws + i, src + (i + 1 - h) * (NS / (2 * h)));
+  }
+}
+
 // L-point DFT across groups of L consecutive lanes (L <= 32, a power of two).
 // In: lane k (= lane % L) holds x[k]. Out: lane k holds X[bitrev_L(k)], with
 // X[f] = sum_k x[k] w^{f k}, w = e^{-2 pi i / L} (conjugated when INV).

@@ -38,6 +38,12 @@ struct Fft {
     fill_stage_table<L>(tab + N, gtw, N);
     for (int i = threadIdx.x; i < E * L; i += blockDim.x) tab[N + 32 + i] = gtw[((i % L) * (i / L)) & (N - 1)];
   }
+  // The same through cp.async (the caller commits and waits).
+  __device__ __forceinline__ static void fill_async(float2* tab, const float2* __restrict__ gtw) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) cp_async8(tab + i, gtw + i);
+    fill_stage_table_async<L>(tab + N, gtw, N);
+    for (int i = threadIdx.x; i < E * L; i += blockDim.x) cp_async8(tab + N + 32 + i, gtw + (((i % L) * (i / L)) & (N - 1)));
+  }
 
   using Net = LaneNet<L, false>;
   __device__ __forceinline__ static void init_net(Net& net, int lane, const float2* __restrict__ tab) {

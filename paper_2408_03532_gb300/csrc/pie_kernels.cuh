@@ -19,6 +19,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "fft_core.cuh"
 #include "pft_core.cuh"
@@ -82,18 +83,15 @@ struct Cluster {
   }
 };
 
-// 4-byte asynchronous global -> shared copies (the amplitudes of a position
-// are fetched while the transforms run).
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
-               "l"(gsrc)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Modulus-projection residual (Eq. 3) and its contribution to the objective.
+// The objective's partial sum is FP64 for the gradient (the loss itself) and
+// FP32 per thread otherwise (at most a few dozen terms; warps add in FP32
+// pairwise, and everything beyond a warp is summed in FP64).
 template <int MODE>
-__device__ __forceinline__ float2 residual(float2 Psi, float d, double& acc) {
+using ResAcc = typename std::conditional<MODE == MODE_GRAD, double, float>::type;
+
+template <int MODE>
+__device__ __forceinline__ float2 residual(float2 Psi, float d, ResAcc<MODE>& acc) {
   const float m2 = cabs2(Psi);
   if (MODE == MODE_GRAD) {
     // sgn(0) = 0; the gradient of sum (|Psi| - d)^2 is 2 R
@@ -109,12 +107,11 @@ __device__ __forceinline__ float2 residual(float2 Psi, float d, double& acc) {
   // theta(0) = 0: a zero coefficient is replaced by d
   float2 R;
   if (m2 > 0.f) {
-    const float m = sqrtf(m2);
-    R = cscale(Psi, 1.f - d / m);
+    R = cscale(Psi, 1.f - d * rsqrtf(m2));
   } else {
     R = make_float2(-d, 0.f);
   }
-  acc += (double)cabs2(R);
+  acc += cabs2(R);
   return R;
 }
 
@@ -205,10 +202,26 @@ __device__ __forceinline__ void accumulate_probe(const PieArgs& a, const PieItem
   atomicAdd(a.pden + pidx, cabs2(zn));
 }
 
-template <int NT>
-__device__ __forceinline__ void block_accumulate(double v, double* red_smem, double* out) {
-  double s = block_sum(v, red_smem);
-  if (threadIdx.x == 0 && s != 0.0) atomicAdd(out, s);
+// The objective's partial sums: each warp writes its share to a shared-memory
+// slot (no barrier), and thread 0 adds the slots to *out after the next
+// block-wide barrier, off the path between projection and adjoint.
+__device__ __forceinline__ void warp_partial(double v, double* red_smem) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red_smem[threadIdx.x >> 5] = v;
+}
+__device__ __forceinline__ void warp_partial(float v, double* red_smem) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red_smem[threadIdx.x >> 5] = (double)v;
+}
+template <int NW>
+__device__ __forceinline__ void flush_partials(const double* red_smem, double* out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) s += red_smem[i];
+    if (s != 0.0) atomicAdd(out, s);
+  }
 }
 
 // ------------------------------------------------------------- PFT variant
@@ -238,7 +251,7 @@ struct PiePftShape {
 };
 
 template <int P, int Q, int MP, int MODE, int C, int NT>
-__global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant__ PftConst c,
+__global__ void __launch_bounds__(NT, (P * Q <= 128 && C >= 4 && Q <= 8) ? 2 : 1) k_pie_pft(PieArgs a, const __grid_constant__ PftConst c,
                                                 const float2* __restrict__ gW, const float2* __restrict__ gtw) {
   using S = PiePftShape<P, Q, MP, C>;
   using T = Pft1D<P, Q, MP>;
@@ -264,6 +277,7 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
   float2 wv[Q], zv[Q];
   auto gather = [&](const PieItem& q) {
     for (int i = threadIdx.x; i < M * CM; i += NT) cp_async4(sD + i, q.dat + rank * CM + (i / CM) * M + (i % CM));
+    cp_async_commit();
     if constexpr (KEEP) {
       const int u = r0 + warp * G + g;
 #pragma unroll
@@ -276,9 +290,14 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
   };
   const int step = gridDim.x / C;
   int it = blockIdx.x / C;
-  if (it < a.count) gather(resolve<M * M>(a, it));
-  for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) sm[i] = gW[i];
-  fill_stage_table<P>(stw, gtw, P);
+  for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) cp_async8(sm + i, gW + i);
+  fill_stage_table_async<P>(stw, gtw, P);
+  cp_async_commit();
+  if (it < a.count)
+    gather(resolve<M * M>(a, it));
+  else
+    cp_async_commit();
+  cp_async_wait_group<1>();  // the tables (the first amplitudes may still be in flight)
   CL::sync();  // every CTA of the cluster has started before any remote store
   LaneNet<P, false> net;
   net.init(k, stw);
@@ -317,12 +336,12 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
     cp_async_wait_all();
     __syncthreads();
     // 3b. modulus projection on the M x CM coefficients
-    double part = 0.0;
+    ResAcc<MODE> part = 0;
     for (int i = threadIdx.x; i < M * CM; i += NT) {
       float2* z = sZ + (i / CM) * S::ZS + (i % CM);
       *z = residual<MODE>(*z, sD[i], part);
     }
-    block_accumulate<NT>(round == 0 ? part : 0.0, sred, p.red);
+    warp_partial(round == 0 ? part : ResAcc<MODE>(0), sred);
     __syncthreads();
     // 3c. adjoint columns -> row owners
     for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
@@ -336,6 +355,7 @@ __global__ void __launch_bounds__(NT) k_pie_pft(PieArgs a, const __grid_constant
       for (int l = 0; l < Q; ++l) dst[(u0 % RN + l) * S::SG + tg] = xv[l];
     }
     CL::sync();
+    if (round == 0) flush_partials<NW>(sred, p.red);
     // 5. adjoint rows and the object update
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int ul = u0 + g, u = r0 + ul;
@@ -379,7 +399,7 @@ struct PieFullShape {
 };
 
 template <int N, int MODE, int C, int NT>
-__global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __restrict__ gtw) {
+__global__ void __launch_bounds__(NT, 2) k_pie_full(PieArgs a, const float2* __restrict__ gtw) {
   using S = PieFullShape<N, C>;
   using F = Fft<N>;
   using CL = Cluster<C>;
@@ -401,6 +421,7 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
   auto gather = [&](const PieItem& q) {
     for (int i = threadIdx.x; i < N * CN; i += NT)
       cp_async4(sD + i, q.dat + F::freq_of_slot(i / CN) * N + F::freq_of_slot(c0 + i % CN));
+    cp_async_commit();
     if constexpr (KEEP) {
       const int u = r0 + warp * G + g;
 #pragma unroll
@@ -413,8 +434,13 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
   };
   const int step = gridDim.x / C;
   int it = blockIdx.x / C;
-  if (it < a.count) gather(resolve<N * N>(a, it));
-  F::fill(tw, gtw);
+  F::fill_async(tw, gtw);
+  cp_async_commit();
+  if (it < a.count)
+    gather(resolve<N * N>(a, it));
+  else
+    cp_async_commit();
+  cp_async_wait_group<1>();  // the tables (the first amplitudes may still be in flight)
   CL::sync();
   typename F::Net net;
   F::init_net(net, l, tw);
@@ -457,12 +483,12 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
     cp_async_wait_all();
     __syncthreads();
     // 3b. modulus projection
-    double part = 0.0;
+    ResAcc<MODE> part = 0;
     for (int i = threadIdx.x; i < N * CN; i += NT) {
       float2* z = sC + (i / CN) * S::SCS + (i % CN);
       *z = residual<MODE>(*z, sD[i], part);
     }
-    block_accumulate<NT>(round == 0 ? part : 0.0, sred, p.red);
+    warp_partial(round == 0 ? part : ResAcc<MODE>(0), sred);
     __syncthreads();
     // 3c. adjoint FFT of the local columns -> row owners (natural row order)
     for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
@@ -478,6 +504,7 @@ __global__ void __launch_bounds__(NT) k_pie_full(PieArgs a, const float2* __rest
       }
     }
     CL::sync();
+    if (round == 0) flush_partials<NW>(sred, p.red);
     // 5. adjoint FFT of this CTA's rows and the object update
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int ul = u0 + g, u = r0 + ul;
