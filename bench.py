@@ -377,7 +377,8 @@ def main() -> None:
     roof = {"bound": "alu", "kernel": dom[0], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
             "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, no measured SIMT peak)",
-            "launches_per_sweep": ncol if mode == pft.MODE_COLOURED else 1,
+            "launches_per_sweep": {"pie_pft": kernel_launches(mode, ncol, tuning, "pft"),
+                                   "pie_full": kernel_launches(mode, ncol, tuning, "full")},
             "sweep_ms": {"pie_pft": k_pft_ms, "pie_full": k_full_ms}}
 
     if rank == 0:
@@ -387,7 +388,9 @@ def main() -> None:
                 cpu = cpu_baseline_block(run_oracle_sample(budget_s=15.0, chunk=128, min_steps=1))
             except Exception as exc:  # report, do not fail the benchmark
                 cpu = {"error": str(exc)[:200]}
-        launches_per_sweep = (ncol + 1) if mode == pft.MODE_COLOURED else 3
+        # PIE kernel launches plus the norms kernel of each sweep (batched mode: + the update)
+        launches_per_sweep = [kernel_launches(mode, ncol, tuning, tr) + (1 if mode == pft.MODE_COLOURED else 2)
+                              for tr in ("pft", "full")]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -395,7 +398,7 @@ def main() -> None:
                 "phase_ms": {"pft_sweep": sum(t_pft) / args.steps, "full_sweep": sum(t_full) / args.steps},
                 "e2e": {"value": world * frames_per_step / (e2e_ms / 1e3), "unit": UNIT,
                         "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-                "gpu_launches": 2 * launches_per_sweep * args.steps,
+                "gpu_launches": sum(launches_per_sweep) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "time_to_target": ttt, "pft_batch": pft_batch, "pft_large": pft_large, "batch64": batch64, "wall_s": wall, "colours": ncol,
                 "autotune": tuning}
@@ -410,6 +413,15 @@ def hbm_peak() -> tuple[float, str]:
         return float(json.load(open(PEAKS_FILE))["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_launches(mode, ncol, tuning, transform):
+    """Launches of the fused PIE kernel per sweep: one per colour, or one for the
+    whole sweep when the autotuner kept the cooperative form (and in batched mode)."""
+    from paper_2408_03532_gb300 import pft
+    if mode != pft.MODE_COLOURED or tuning.get(f"persistent_{transform}"):
+        return 1
+    return ncol
 
 
 def measure_pft_batch(pft, torch, dev, stream, flush, frames: int = 4096, n: int = 256, reps: int = 5) -> dict:

@@ -193,7 +193,11 @@ typedef struct pie_problem {
   double delta_rel;      /* batched mode: delta = delta_rel * max illumination */
   int autotune;          /* 1: time every built kernel variant (CTAs per position)
                             on a scratch object at creation and keep the fastest;
-                            0: pick by occupancy                                  */
+                            in coloured mode also the same kernel run as one
+                            cooperative launch per sweep (a grid barrier between
+                            colours, bounded at 2 s: a timeout is returned as
+                            PFT_ERR_TIMEOUT by the next pie_iteration);
+                            0: pick by occupancy, one launch per colour           */
 } pie_problem;
 
 typedef struct pie_stats {
@@ -213,6 +217,8 @@ typedef struct pie_ctx_info {
   int p, q, r;
   int cluster_pft, cluster_full;
   double sweep_ms_pft, sweep_ms_full;
+  int persistent_pft, persistent_full;  /* 1: coloured sweeps run as one
+                                           cooperative launch per sweep */
 } pie_ctx_info;
 
 int pie_ctx_info_get(const pie_ctx* ctx, pie_ctx_info* info);
@@ -296,6 +302,16 @@ int pie_tv_step(pie_ctx* ctx, void* object, double lambda, double eps, void* str
  * re-coloured greedily in that order and every sweep then runs colour-major
  * with that order inside each colour. Synchronises the device. */
 int pie_ctx_set_order(pie_ctx* ctx, const int32_t* order);
+
+/* How coloured sweeps of `transform` are launched: persistent = 1 runs the
+ * whole sweep as one cooperative launch (the fused kernel loops over the
+ * colours with a grid barrier in between; as many clusters as fit on the GPU
+ * at once), 0 one launch per colour. Results are identical either way (the
+ * colour order and the per-position arithmetic do not change). The
+ * autotuner sets this at creation; UNSUPPORTED in batched mode or when the
+ * transform is not built. If the device refuses the cooperative launch, the
+ * next sweep falls back to one launch per colour (pie_ctx_info_get shows it). */
+int pie_ctx_set_persistent(pie_ctx* ctx, int transform, int persistent);
 
 /* Phase-aligned error min_phi ||e^{i phi} z - truth|| / ||truth|| over the
  * context's illuminated mask (FP64 on the GPU); synchronises `stream`. */

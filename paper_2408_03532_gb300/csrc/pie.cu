@@ -244,6 +244,12 @@ struct pie_ctx {
   std::vector<int> colour, col_off, visit;
   int ncol = 0;
   int* d_sched = nullptr;
+  int* d_coloff = nullptr;     // colour offsets into d_sched [ncol + 1] (persistent sweeps)
+  int max_colour = 0;          // positions in the largest colour
+  unsigned* d_gbar = nullptr;  // [2]: grid-barrier arrivals, error word
+  int* h_gstatus = nullptr;    // mapped host status word of the persistent sweeps
+  int* d_gstatus = nullptr;
+  bool persist[2] = {false, false};  // coloured sweeps as one cooperative launch (autotuned)
   float* d_inv_illum = nullptr;
   unsigned char* d_mask = nullptr;
   float2* d_prev = nullptr;
@@ -347,6 +353,13 @@ int upload_schedule(pie_ctx* c, cudaStream_t st) {
   std::vector<int> fill(c->col_off.begin(), c->col_off.end() - 1);
   for (int j : c->visit) sched[fill[c->colour[j]]++] = j;
   PFT_CUDA_TRY(cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(int) * c->npos, cudaMemcpyHostToDevice, st));
+  cudaFree(c->d_coloff);
+  c->d_coloff = nullptr;
+  PFT_CUDA_TRY(cudaMalloc(&c->d_coloff, sizeof(int) * c->col_off.size()));
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_coloff, c->col_off.data(), sizeof(int) * c->col_off.size(),
+                               cudaMemcpyHostToDevice, st));
+  c->max_colour = 0;
+  for (int k = 0; k < c->ncol; ++k) c->max_colour = std::max(c->max_colour, c->col_off[k + 1] - c->col_off[k]);
   PFT_CUDA_TRY(cudaStreamSynchronize(st));
   return PFT_OK;
 }
@@ -395,6 +408,58 @@ int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) 
   return PFT_OK;
 }
 
+// One coloured sweep as a single cooperative launch: as many clusters as fit
+// on the GPU at once (at most the largest colour), looping over the colours
+// with a grid barrier in between (same kernel as the per-colour launches).
+// Cluster size (log2) of a persistent coloured sweep: the autotuned one, else
+// the largest built (-1: none).
+int persist_ci(const pie_ctx* c, int t) {
+  if (c->tuned[t][MODE_COLOURED] >= 0) return c->tuned[t][MODE_COLOURED];
+  for (int q = 3; q >= 0; --q)
+    if (c->kern[t][MODE_COLOURED][q].fn) return q;
+  return -1;
+}
+
+int launch_pie_persistent(pie_ctx* c, int transform, PieArgs a, cudaStream_t st) {
+  const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
+  const int ci = persist_ci(c, t);
+  if (ci < 0) return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for this transform");
+  const PieKernel& k = c->kern[t][MODE_COLOURED][ci];
+  if (!k.fn) return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for this transform");
+  const long long clusters =
+      std::max<long long>(1, std::min<long long>(c->max_colour, c->cap[t][MODE_COLOURED][ci] / k.cluster));
+  a.list = c->d_sched;
+  a.count = 0;
+  a.col_off = c->d_coloff;
+  a.ncol = c->ncol;
+  a.gbar = c->d_gbar;
+  a.gerr = reinterpret_cast<int*>(c->d_gbar + 1);
+  a.gstatus = c->d_gstatus;
+  PFT_CUDA_TRY(cudaMemsetAsync(c->d_gbar, 0, 2 * sizeof(unsigned), st));
+  PftConst cst = c->plan.cst;
+  const float2* W = c->plan.d_W;
+  const float2* tw = t == 0 ? c->plan.d_twp : pfth::twiddles(c->n);
+  if (!tw) return PFT_ERR_CUDA;
+  void* args_pft[] = {(void*)&a, (void*)&cst, (void*)&W, (void*)&tw};
+  void* args_full[] = {(void*)&a, (void*)&tw};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * k.cluster));
+  cfg.blockDim = dim3(k.threads);
+  cfg.dynamicSmemBytes = k.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = k.cluster;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = k.cluster > 1 ? 2 : 1;
+  PFT_CUDA_TRY(cudaLaunchKernelExC(&cfg, k.fn, t == 0 ? args_pft : args_full));
+  return PFT_OK;
+}
+
 int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st,
                   double gamma = -1.0, int mode = -1);
 
@@ -437,6 +502,28 @@ int autotune(pie_ctx* c, cudaStream_t st) {
     }
     c->tuned[t][mode] = best;
     c->tuned_ms[t] = best >= 0 ? best_ms / 2.0 : 0.0;
+    // coloured sweeps: the same kernel as one cooperative launch per sweep
+    if (rc == PFT_OK && best >= 0 && mode == MODE_COLOURED && c->d_gbar) {
+      c->persist[t] = true;
+      k_fill<<<grid_for(HW), kThreads, 0, st>>>(scratch, HW, make_float2(0.7f, 0.2f));
+      int prc = enqueue_sweep(c, scratch, tr, 1.0, false, st);
+      if (prc == PFT_OK) {
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 2 && prc == PFT_OK; ++rep) prc = enqueue_sweep(c, scratch, tr, 1.0, false, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) prc = PFT_ERR_CUDA;
+      }
+      float ms = 0.f;
+      if (prc == PFT_OK) cudaEventElapsedTime(&ms, e0, e1);
+      if (prc != PFT_OK || *c->h_gstatus != PFT_OK || !(ms < best_ms)) {
+        c->persist[t] = false;
+        *c->h_gstatus = PFT_OK;
+        cudaGetLastError();  // a refused cooperative launch is not sticky
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = pfth::set_error(PFT_ERR_CUDA, "autotune sweep failed");
+      } else {
+        c->tuned_ms[t] = ms / 2.0;
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -459,6 +546,9 @@ int pie_ctx_destroy(pie_ctx* c) {
   cudaFree(c->d_amp);
   cudaFree(c->d_ampc);
   cudaFree(c->d_sched);
+  cudaFree(c->d_coloff);
+  cudaFree(c->d_gbar);
+  if (c->h_gstatus) cudaFreeHost(c->h_gstatus);
   cudaFree(c->d_inv_illum);
   cudaFree(c->d_mask);
   cudaFree(c->d_prev);
@@ -590,6 +680,10 @@ int pie_ctx_create(pie_ctx** out, const pie_problem* pb, const void* probe, cons
                                                     (float)(pb->delta_rel > 0 ? pb->delta_rel : 1e-3), c->d_mask);
   PIE_CUDA(cudaGetLastError());
   PIE_CUDA(cudaStreamSynchronize(st));
+  PIE_CUDA(cudaMalloc(&c->d_gbar, 2 * sizeof(unsigned)));
+  PIE_CUDA(cudaHostAlloc(&c->h_gstatus, sizeof(int), cudaHostAllocMapped));
+  *c->h_gstatus = PFT_OK;
+  PIE_CUDA(cudaHostGetDevicePointer(&c->d_gstatus, c->h_gstatus, 0));
   if (pb->autotune) PIE_TRY(autotune(c, st));
 #undef PIE_TRY
 #undef PIE_CUDA
@@ -608,6 +702,8 @@ int pie_ctx_info_get(const pie_ctx* c, pie_ctx_info* info) {
   info->cluster_full = c->tuned[1][mode] >= 0 ? (1 << c->tuned[1][mode]) : 0;
   info->sweep_ms_pft = c->tuned_ms[0];
   info->sweep_ms_full = c->tuned_ms[1];
+  info->persistent_pft = c->persist[0] ? 1 : 0;
+  info->persistent_full = c->persist[1] ? 1 : 0;
   return PFT_OK;
 }
 
@@ -658,7 +754,11 @@ int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stat
       k_probe_init<<<1, 1024, 0, st>>>(c->d_probe, n2i, c->d_pacc, c->d_pden, c->d_pscale);
       PFT_CUDA_TRY(cudaGetLastError());
     }
-    for (int col = 0; col < c->ncol; ++col) {
+    if (!blind && c->persist[transform == PIE_TRANSFORM_PFT ? 0 : 1]) {
+      int rc = launch_pie_persistent(c, transform, a, st);
+      if (rc != PFT_OK) return rc;
+    }
+    for (int col = 0; col < c->ncol && (blind || !c->persist[transform == PIE_TRANSFORM_PFT ? 0 : 1]); ++col) {
       a.list = c->d_sched + c->col_off[col];
       a.count = c->col_off[col + 1] - c->col_off[col];
       int rc = launch_pie(c, transform, MODE_COLOURED, a, st);
@@ -697,19 +797,29 @@ int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats,
       *out = g.exec;
       return PFT_OK;
     }
-  PFT_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_sweep(c, obj, transform, beta, stats, c->cap_stream, gamma, mode);
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
-  if (rc != PFT_OK) {
-    if (graph) cudaGraphDestroy(graph);
-    return rc;
-  }
-  if (e != cudaSuccess) return pfth::cuda_error(e, "cudaStreamEndCapture");
   cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return pfth::cuda_error(e, "cudaGraphInstantiate");
+  const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
+  for (int attempt = 0;; ++attempt) {
+    PFT_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_sweep(c, obj, transform, beta, stats, c->cap_stream, gamma, mode);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (rc == PFT_OK && e == cudaSuccess) {
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e == cudaSuccess) break;
+    } else if (graph) {
+      cudaGraphDestroy(graph);
+    }
+    // a cooperative launch that cannot be captured: per-colour launches instead
+    if (attempt == 0 && c->persist[t] && gamma < 0.0 && mode == PIE_MODE_COLOURED) {
+      cudaGetLastError();
+      c->persist[t] = false;
+      continue;
+    }
+    if (rc != PFT_OK) return rc;
+    return pfth::cuda_error(e, "sweep graph capture");
+  }
   if (c->graphs.size() >= 8) {
     cudaGraphExecDestroy(c->graphs.front().exec);
     c->graphs.erase(c->graphs.begin());
@@ -731,6 +841,11 @@ int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, 
     return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
   if (transform == PIE_TRANSFORM_FULL && !c->have_full)
     return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n in {16, 32, 64, 128}, not %d", c->n);
+  if (c->h_gstatus && *c->h_gstatus != PFT_OK) {
+    const int e = *c->h_gstatus;
+    *c->h_gstatus = PFT_OK;
+    return pfth::set_error(e, "a grid barrier of an earlier persistent sweep timed out");
+  }
   cudaStream_t st = (cudaStream_t)stream;
   if (gamma >= 0.0) {
     if (mode != PIE_MODE_COLOURED)
@@ -808,6 +923,25 @@ int pie_tv_step(pie_ctx* c, void* object, double lambda, double eps, void* strea
   PFT_CUDA_TRY(cudaMemcpyAsync(c->d_tv, object, sizeof(float2) * HW, cudaMemcpyDeviceToDevice, st));
   k_tv_step<<<grid_for(HW), kThreads, 0, st>>>(c->d_tv, (float2*)object, c->H, c->W, (float)lambda, (float)eps);
   PFT_CUDA_TRY(cudaGetLastError());
+  return PFT_OK;
+}
+
+int pie_ctx_set_persistent(pie_ctx* c, int transform, int persistent) {
+  if (!c) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
+  const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
+  if (c->pb.mode != PIE_MODE_COLOURED)
+    return pfth::set_error(PFT_ERR_UNSUPPORTED, "persistent sweeps are built for coloured mode");
+  if (t == 1 && !c->have_full) return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is not built for this n");
+  if (persistent && persist_ci(c, t) < 0)
+    return pfth::set_error(PFT_ERR_UNSUPPORTED, "no kernel for a persistent sweep");
+  if (c->persist[t] != (persistent != 0)) {
+    PFT_CUDA_TRY(cudaDeviceSynchronize());
+    c->persist[t] = persistent != 0;
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+  }
   return PFT_OK;
 }
 

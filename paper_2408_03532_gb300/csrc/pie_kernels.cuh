@@ -64,6 +64,13 @@ struct PieArgs {
   float2* pacc;             // sum conj(z_new) dpsi' over the colour (null = non-blind)
   float* pden;              // sum |z_new|^2 over the colour
   const float* pscale;      // max |w|^2 of the current probe (divides coef when set)
+  // persistent coloured sweep (ncol > 0): one launch runs every colour; colour
+  // k is list[col_off[k] .. col_off[k + 1]), with a grid barrier in between
+  const int* col_off;
+  int ncol;
+  unsigned* gbar;           // arrival counter, zero at launch
+  int* gerr;                // set when a barrier gives up (device word, zero at launch)
+  int* gstatus;             // mapped host status word: PFT_ERR_TIMEOUT on a timeout
 };
 
 template <int C>
@@ -82,6 +89,47 @@ struct Cluster {
     else return cg::this_cluster().map_shared_rank(p, r);
   }
 };
+
+// Grid-wide barrier of a co-resident (cooperative) launch: every CTA makes its
+// writes visible GPU-wide, adds one to *ctr and waits until it reaches
+// `target` (CTAs x barriers so far). The wait is bounded: after 2 s, or as
+// soon as another CTA has given up, it returns false (a timeout also sets the
+// error words). One arrival per CTA measured faster than one per cluster
+// behind two cluster barriers.
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* gerr, int* gstatus) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    int ok = 1;
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
+      if (*reinterpret_cast<volatile int*>(gerr)) {
+        ok = 0;
+        break;
+      }
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > 2000000000ull) {
+        atomicExch(gerr, 1);
+        if (gstatus) {
+          *reinterpret_cast<volatile int*>(gstatus) = PFT_ERR_TIMEOUT;
+          __threadfence_system();
+        }
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
 
 // Modulus-projection residual (Eq. 3) and its contribution to the objective.
 // The objective's partial sum is FP64 for the gradient (the loss itself) and
@@ -165,7 +213,7 @@ template <int MODE>
 __device__ __forceinline__ void apply_update(const PieArgs& a, const PieItem& p, long long oidx, float2 w,
                                              float2 dpsi, int pidx) {
   if (MODE == MODE_COLOURED) {
-    float2 o = p.obj[oidx];
+    float2 o = __ldcg(p.obj + oidx);  // L2: a persistent sweep's other CTAs wrote it
     const float2 u = cmulc(dpsi, w);  // conj(w) dpsi
     o.x = fmaf(-p.coef, u.x, o.x);
     o.y = fmaf(-p.coef, u.y, o.y);
@@ -275,38 +323,54 @@ __global__ void __launch_bounds__(NT, (P * Q <= 128 && C >= 4 && Q <= 8) ? 2 : 1
   // item's are loaded as soon as the current one is done.
   constexpr bool KEEP = (RN == NW * G);
   float2 wv[Q], zv[Q];
-  auto gather = [&](const PieItem& q) {
+  auto gather_static = [&](const PieItem& q) {
     for (int i = threadIdx.x; i < M * CM; i += NT) cp_async4(sD + i, q.dat + rank * CM + (i / CM) * M + (i % CM));
     cp_async_commit();
     if constexpr (KEEP) {
       const int u = r0 + warp * G + g;
 #pragma unroll
-      for (int l = 0; l < Q; ++l) {
-        const int v = Q * k + l;
-        wv[l] = __ldg(q.probe + u * N + v);
-        zv[l] = q.objr[q.obase + (long long)u * q.obj_w + v];
-      }
+      for (int l = 0; l < Q; ++l) wv[l] = __ldg(q.probe + u * N + Q * k + l);
+    }
+  };
+  auto gather_obj = [&](const PieItem& q) {
+    if constexpr (KEEP) {
+      const int u = r0 + warp * G + g;
+#pragma unroll
+      for (int l = 0; l < Q; ++l) zv[l] = __ldcg(q.objr + q.obase + (long long)u * q.obj_w + Q * k + l);
     }
   };
   const int step = gridDim.x / C;
-  int it = blockIdx.x / C;
+  const int ncol = a.ncol > 0 ? a.ncol : 1;
+  int ce = a.ncol > 0 ? a.col_off[1] : a.count;
+  int it = (a.ncol > 0 ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
   for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) cp_async8(sm + i, gW + i);
   fill_stage_table_async<P>(stw, gtw, P);
   cp_async_commit();
-  if (it < a.count)
-    gather(resolve<M * M>(a, it));
-  else
+  if (it < ce) {
+    const PieItem q = resolve<M * M>(a, it);
+    gather_static(q);
+    gather_obj(q);
+  } else {
     cp_async_commit();
+  }
   cp_async_wait_group<1>();  // the tables (the first amplitudes may still be in flight)
   CL::sync();  // every CTA of the cluster has started before any remote store
   LaneNet<P, false> net;
   net.init(k, stw);
   const int rounds = (MODE == MODE_COLOURED && a.pacc) ? 2 : 1;
-  for (; it < a.count; it += step) {
+  for (int col = 0; col < ncol; ++col) {
+  if (col > 0) {
+    if (!grid_barrier(a.gbar, (unsigned)col * gridDim.x, a.gerr, a.gstatus)) break;
+    if (it < ce) gather_obj(resolve<M * M>(a, it));
+  }
+  for (; it < ce; it += step) {
     const PieItem p = resolve<M * M>(a, it);
     const long long obase = p.obase;
     for (int round = 0; round < rounds; ++round) {
-    if (KEEP && round == 1) gather(p);  // the updated patch
+    if (KEEP && round == 1) {  // the updated patch
+      gather_static(p);
+      gather_obj(p);
+    }
     // 1. rows (axis 2) of the exit wave -> column owners
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int u = r0 + u0 + g;
@@ -317,7 +381,7 @@ __global__ void __launch_bounds__(NT, (P * Q <= 128 && C >= 4 && Q <= 8) ? 2 : 1
         if constexpr (KEEP)
           xv[l] = cmul(wv[l], zv[l]);
         else
-          xv[l] = cmul(__ldg(p.probe + u * N + v), p.objr[obase + (long long)u * p.obj_w + v]);
+          xv[l] = cmul(__ldg(p.probe + u * N + v), __ldcg(p.objr + obase + (long long)u * p.obj_w + v));
       }
       T::forward(xv, k, c.bh[1], sW2, net, [&](int t, float2 val) {
         float2* dst = CL::map(sY, (unsigned)(t / CM));
@@ -377,9 +441,22 @@ __global__ void __launch_bounds__(NT, (P * Q <= 128 && C >= 4 && Q <= 8) ? 2 : 1
     }
     if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
     }  // round
-    if (it + step < a.count) gather(resolve<M * M>(a, it + step));
+    if (it + step < ce) {  // the next item of this colour
+      const PieItem q = resolve<M * M>(a, it + step);
+      gather_static(q);
+      gather_obj(q);
+    }
     if constexpr (C == 1) __syncthreads();
   }
+  if (col + 1 < ncol) {  // the next colour's first item: all but the object before the barrier
+    ce = a.col_off[col + 2];
+    it = a.col_off[col + 1] + (int)(blockIdx.x / C);
+    if (it < ce)
+      gather_static(resolve<M * M>(a, it));
+    else
+      cp_async_commit();
+  }
+  }  // colour
 }
 
 // ------------------------------------------------------------ FFT variant
@@ -418,38 +495,54 @@ __global__ void __launch_bounds__(NT, 2) k_pie_full(PieArgs a, const float2* __r
   // values stay in registers from the exit wave to the update.
   constexpr bool KEEP = (RN == NW * G);
   float2 wv[E], zv[E];
-  auto gather = [&](const PieItem& q) {
+  auto gather_static = [&](const PieItem& q) {
     for (int i = threadIdx.x; i < N * CN; i += NT)
       cp_async4(sD + i, q.dat + F::freq_of_slot(i / CN) * N + F::freq_of_slot(c0 + i % CN));
     cp_async_commit();
     if constexpr (KEEP) {
       const int u = r0 + warp * G + g;
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int v = l + L * e;
-        wv[e] = __ldg(q.probe + u * N + v);
-        zv[e] = q.objr[q.obase + (long long)u * q.obj_w + v];
-      }
+      for (int e = 0; e < E; ++e) wv[e] = __ldg(q.probe + u * N + l + L * e);
+    }
+  };
+  auto gather_obj = [&](const PieItem& q) {
+    if constexpr (KEEP) {
+      const int u = r0 + warp * G + g;
+#pragma unroll
+      for (int e = 0; e < E; ++e) zv[e] = __ldcg(q.objr + q.obase + (long long)u * q.obj_w + l + L * e);
     }
   };
   const int step = gridDim.x / C;
-  int it = blockIdx.x / C;
+  const int ncol = a.ncol > 0 ? a.ncol : 1;
+  int ce = a.ncol > 0 ? a.col_off[1] : a.count;
+  int it = (a.ncol > 0 ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
   F::fill_async(tw, gtw);
   cp_async_commit();
-  if (it < a.count)
-    gather(resolve<N * N>(a, it));
-  else
+  if (it < ce) {
+    const PieItem q = resolve<N * N>(a, it);
+    gather_static(q);
+    gather_obj(q);
+  } else {
     cp_async_commit();
+  }
   cp_async_wait_group<1>();  // the tables (the first amplitudes may still be in flight)
   CL::sync();
   typename F::Net net;
   F::init_net(net, l, tw);
   const int rounds = (MODE == MODE_COLOURED && a.pacc) ? 2 : 1;
-  for (; it < a.count; it += step) {
+  for (int col = 0; col < ncol; ++col) {
+  if (col > 0) {
+    if (!grid_barrier(a.gbar, (unsigned)col * gridDim.x, a.gerr, a.gstatus)) break;
+    if (it < ce) gather_obj(resolve<N * N>(a, it));
+  }
+  for (; it < ce; it += step) {
     const PieItem p = resolve<N * N>(a, it);
     const long long obase = p.obase;
     for (int round = 0; round < rounds; ++round) {
-    if (KEEP && round == 1) gather(p);  // the updated patch
+    if (KEEP && round == 1) {  // the updated patch
+      gather_static(p);
+      gather_obj(p);
+    }
     // 1. FFT of this CTA's rows of the exit wave -> column-slot owners
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
       const int u = r0 + u0 + g;
@@ -460,7 +553,7 @@ __global__ void __launch_bounds__(NT, 2) k_pie_full(PieArgs a, const float2* __r
         if constexpr (KEEP)
           x[e] = cmul(wv[e], zv[e]);
         else
-          x[e] = cmul(__ldg(p.probe + u * N + v), p.objr[obase + (long long)u * p.obj_w + v]);
+          x[e] = cmul(__ldg(p.probe + u * N + v), __ldcg(p.objr + obase + (long long)u * p.obj_w + v));
       }
       F::fwd(x, l, tw, net);
 #pragma unroll
@@ -528,9 +621,22 @@ __global__ void __launch_bounds__(NT, 2) k_pie_full(PieArgs a, const float2* __r
     }
     if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
     }  // round
-    if (it + step < a.count) gather(resolve<N * N>(a, it + step));
+    if (it + step < ce) {  // the next item of this colour
+      const PieItem q = resolve<N * N>(a, it + step);
+      gather_static(q);
+      gather_obj(q);
+    }
     if constexpr (C == 1) __syncthreads();
   }
+  if (col + 1 < ncol) {  // the next colour's first item: all but the object before the barrier
+    ce = a.col_off[col + 2];
+    it = a.col_off[col + 1] + (int)(blockIdx.x / C);
+    if (it < ce)
+      gather_static(resolve<N * N>(a, it));
+    else
+      cp_async_commit();
+  }
+  }  // colour
 }
 
 // ---------------------------------------------------------------- registry

@@ -48,7 +48,8 @@ class PieProblem(ctypes.Structure):
 class PieCtxInfo(ctypes.Structure):
     _fields_ = [("ncolours", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int), ("r", ctypes.c_int),
                 ("cluster_pft", ctypes.c_int), ("cluster_full", ctypes.c_int),
-                ("sweep_ms_pft", ctypes.c_double), ("sweep_ms_full", ctypes.c_double)]
+                ("sweep_ms_pft", ctypes.c_double), ("sweep_ms_full", ctypes.c_double),
+                ("persistent_pft", ctypes.c_int), ("persistent_full", ctypes.c_int)]
 
 
 class PieStats(ctypes.Structure):
@@ -113,6 +114,7 @@ def load() -> ctypes.CDLL:
         "pie_nrmse": (ctypes.c_int, [_P, _P, _P, _P, _P]),
         "pie_tv_step": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, _P]),
         "pie_ctx_set_order": (ctypes.c_int, [_P, _P]),
+        "pie_ctx_set_persistent": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
         "pie_amp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
         "pie_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
@@ -344,6 +346,10 @@ class PieContext:
         if o.shape != (self.npos,):
             raise ValueError("order must be a permutation of the positions")
         _check(load().pie_ctx_set_order(self._h, o.ctypes.data))
+
+    def set_persistent(self, transform: int, persistent: bool = True):
+        """Coloured sweeps of `transform` as one cooperative launch (True) or one launch per colour."""
+        _check(load().pie_ctx_set_persistent(self._h, transform, 1 if persistent else 0))
 
     def iteration_blind(self, obj, transform: int = TRANSFORM_FULL, beta: float = 1.0, gamma: float = 1.0,
                         stats: bool = True, stream=None):

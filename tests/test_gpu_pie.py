@@ -55,6 +55,18 @@ def mid():
     return synth.spiral_problem(side=384, n=128, count=100, peak_photons=1e4, M=32)
 
 
+@pytest.fixture(scope="module")
+def wide_colours():
+    """Two interleaved 30 x 30 rasters of 32^2 patches (stride 33) on a 1024^2
+    object: 2 colours of 900 positions each, more than the clusters that fit on
+    the GPU at once."""
+    obj = synth.make_object(1024)
+    probe = synth.make_probe(32)
+    pos = np.concatenate([synth.raster_scan(30, 30, 33, 2), synth.raster_scan(30, 30, 33, 18)])
+    return dict(obj=obj, probe=probe, pos=pos, intensities=synth.simulate_intensities(obj, probe, pos), M=16,
+                init=synth.random_init(1024))
+
+
 def test_colouring_matches_oracle(env, small, mid):
     torch, pft = env
     for P in (small, mid):
@@ -80,6 +92,36 @@ def test_coloured_sweep_matches_oracle(env, small, mid, transform, which):
     assert rel(z.cpu().numpy(), zo) < TOL
     assert st["phi"] == pytest.approx(phi, rel=TOL)
     assert st["rel_change"] == pytest.approx(opie.relative_change(zo, P["init"]), rel=1e-4)
+
+
+@pytest.mark.parametrize("transform", ["pft", "full"])
+@pytest.mark.parametrize("which", ["mid", "wide"])
+def test_persistent_sweep_matches_per_colour_launches(env, mid, wide_colours, transform, which):
+    """A coloured sweep as one cooperative launch (grid barrier between colours)
+    gives the same object, bit for bit, as one launch per colour."""
+    torch, pft = env
+    P = mid if which == "mid" else wide_colours
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    a, b = make_ctx(P, torch, pft), make_ctx(P, torch, pft)
+    a.set_persistent(tr, False)
+    b.set_persistent(tr, True)
+    za, zb = c64(P["init"], torch), c64(P["init"], torch)
+    for _ in range(2):
+        sa = a.iteration(za, tr, 0.9)
+        sb = b.iteration(zb, tr, 0.9)
+    assert b.info()[f"persistent_{transform}"] == 1
+    assert a.info()[f"persistent_{transform}"] == 0
+    assert torch.equal(za, zb)
+    assert sb["phi"] == pytest.approx(sa["phi"], rel=1e-6)
+    if which == "wide":
+        assert len(np.unique(b.colours())) == 2
+        zc = c64(P["init"], torch)
+        b.iteration(zc, tr, 0.9, stats=False)
+        T, d = oracle_T(P, transform)
+        n = P["probe"].shape[0]
+        order = opie.colour_major_order(opie.greedy_colouring(P["pos"], n, n))
+        zo, _ = opie.pie_sweep(P["init"], P["probe"], P["pos"], d, T, 0.9, order)
+        assert rel(zc.cpu().numpy(), zo) < TOL
 
 
 @pytest.mark.parametrize("transform", ["pft", "full"])
