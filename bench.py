@@ -237,6 +237,9 @@ def main() -> None:
     ap.add_argument("--no-pft-batch", action="store_true")
     ap.add_argument("--pft-frames", type=int, default=4096)
     ap.add_argument("--no-batch64", action="store_true")
+    ap.add_argument("--sweep-launch", choices=["auto", "persistent", "per-colour"], default="auto",
+                    help="coloured sweeps as one cooperative launch or one launch per colour (auto: the "
+                         "autotuner's choice; with --no-autotune, per colour)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the built-in cluster-size heuristic instead of timing each size (for profilers, "
                          "whose per-launch overhead distorts the autotuner's timings)")
@@ -289,6 +292,9 @@ def main() -> None:
     ctx = pft.PieContext((H, W), probe, P["pos"], inten, M=M, mode=mode, autotune=not args.no_autotune)
     del inten
     ncol = int(ctx.colours().max()) + 1
+    if args.sweep_launch != "auto" and mode == pft.MODE_COLOURED:
+        for tr in (pft.TRANSFORM_PFT, pft.TRANSFORM_FULL):
+            ctx.set_persistent(tr, args.sweep_launch == "persistent")
     tuning = ctx.info()
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -301,6 +307,7 @@ def main() -> None:
     for _ in range(args.warmup):
         step(z)
     torch.cuda.synchronize()
+    tuning = ctx.info()  # after the first captures (a refused cooperative launch falls back per colour)
 
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     barrier(world)
