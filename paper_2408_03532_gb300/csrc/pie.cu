@@ -742,6 +742,7 @@ int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stat
   a.dat = transform == PIE_TRANSFORM_PFT ? c->d_ampc : c->d_amp;
   a.gprobe = nullptr;
   a.red = c->d_red;
+  a.gstatus = c->d_gstatus;
   if (mode == PIE_MODE_COLOURED) {
     a.coef = (float)(beta / ((double)c->probe_max2 * n2));
     a.acc = nullptr;
@@ -844,7 +845,8 @@ int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, 
   if (c->h_gstatus && *c->h_gstatus != PFT_OK) {
     const int e = *c->h_gstatus;
     *c->h_gstatus = PFT_OK;
-    return pfth::set_error(e, "a grid barrier of an earlier persistent sweep timed out");
+    return pfth::set_error(e, e == PFT_ERR_TIMEOUT ? "a grid barrier of an earlier persistent sweep timed out"
+                                                   : "an earlier sweep's kernel ran without its cluster shape");
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (gamma >= 0.0) {

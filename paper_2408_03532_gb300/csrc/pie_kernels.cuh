@@ -90,6 +90,22 @@ struct Cluster {
   }
 };
 
+// A cluster kernel launched without its cluster shape must not address peer
+// shared memory: it records an error and does nothing.
+template <int C>
+__device__ __forceinline__ bool cluster_shape_ok(int* gstatus) {
+  if constexpr (C > 1) {
+    if (cg::this_cluster().num_blocks() != (unsigned)C) {
+      if (threadIdx.x == 0 && gstatus) {
+        *reinterpret_cast<volatile int*>(gstatus) = PFT_ERR_CUDA;
+        __threadfence_system();
+      }
+      return false;
+    }
+  }
+  return true;
+}
+
 // Grid-wide barrier of a co-resident (cooperative) launch: every CTA makes its
 // writes visible GPU-wide, adds one to *ctr and waits until it reaches
 // `target` (CTAs x barriers so far). The wait is bounded: after 2 s, or as
@@ -314,6 +330,7 @@ __global__ void __launch_bounds__(NT, (P * Q <= 128 && C >= 4 && Q <= 8) ? 2 : 1
   float2* sZ = sm + S::OFF_Z;
   double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
   float* sD = reinterpret_cast<float*>(sm + S::OFF_D);
+  if (!cluster_shape_ok<C>(a.gstatus)) return;
   const unsigned rank = CL::rank();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = lane % P, g = lane / P;
@@ -487,6 +504,7 @@ __global__ void __launch_bounds__(NT, 2) k_pie_full(PieArgs a, const float2* __r
   float2* sR = sm + S::OFF_R;
   double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
   float* sD = reinterpret_cast<float*>(sm + S::OFF_D);
+  if (!cluster_shape_ok<C>(a.gstatus)) return;
   const unsigned rank = CL::rank();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int l = lane % L, g = lane / L;
