@@ -288,6 +288,15 @@ __device__ __forceinline__ void flush_partials(const double* red_smem, double* o
   }
 }
 
+// Resident CTAs per SM the kernels are compiled for (a register budget): a
+// coloured sweep's cluster kernels need two per SM so that every position of a
+// colour is on the GPU at once; the batched and gradient sweeps run two
+// (three measured the same, with more spills). Shapes with more than 8 values
+// per lane or frames above 128 keep the compiler's choice.
+constexpr int pie_min_blocks(int mode, int C, int n, int q) {
+  return (n > 128 || q > 8) ? 1 : mode == MODE_COLOURED ? (C >= 4 ? 2 : 1) : 2;
+}
+
 // ------------------------------------------------------------- PFT variant
 template <int P, int Q, int MP, int C>
 struct PiePftShape {
@@ -315,7 +324,7 @@ struct PiePftShape {
 };
 
 template <int P, int Q, int MP, int MODE, int C, int NT>
-__global__ void __launch_bounds__(NT, (P * Q <= 128 && C >= 4 && Q <= 8) ? 2 : 1) k_pie_pft(PieArgs a, const __grid_constant__ PftConst c,
+__global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_pft(PieArgs a, const __grid_constant__ PftConst c,
                                                 const float2* __restrict__ gW, const float2* __restrict__ gtw) {
   using S = PiePftShape<P, Q, MP, C>;
   using T = Pft1D<P, Q, MP>;
@@ -357,9 +366,10 @@ __global__ void __launch_bounds__(NT, (P * Q <= 128 && C >= 4 && Q <= 8) ? 2 : 1
     }
   };
   const int step = gridDim.x / C;
-  const int ncol = a.ncol > 0 ? a.ncol : 1;
-  int ce = a.ncol > 0 ? a.col_off[1] : a.count;
-  int it = (a.ncol > 0 ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
+  const bool persistent = MODE == MODE_COLOURED && a.ncol > 0;  // every colour in this launch
+  const int ncol = persistent ? a.ncol : 1;
+  int ce = persistent ? a.col_off[1] : a.count;
+  int it = (persistent ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
   for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) cp_async8(sm + i, gW + i);
   fill_stage_table_async<P>(stw, gtw, P);
   cp_async_commit();
@@ -493,7 +503,7 @@ struct PieFullShape {
 };
 
 template <int N, int MODE, int C, int NT>
-__global__ void __launch_bounds__(NT, 2) k_pie_full(PieArgs a, const float2* __restrict__ gtw) {
+__global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(PieArgs a, const float2* __restrict__ gtw) {
   using S = PieFullShape<N, C>;
   using F = Fft<N>;
   using CL = Cluster<C>;
@@ -531,9 +541,10 @@ __global__ void __launch_bounds__(NT, 2) k_pie_full(PieArgs a, const float2* __r
     }
   };
   const int step = gridDim.x / C;
-  const int ncol = a.ncol > 0 ? a.ncol : 1;
-  int ce = a.ncol > 0 ? a.col_off[1] : a.count;
-  int it = (a.ncol > 0 ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
+  const bool persistent = MODE == MODE_COLOURED && a.ncol > 0;  // every colour in this launch
+  const int ncol = persistent ? a.ncol : 1;
+  int ce = persistent ? a.col_off[1] : a.count;
+  int it = (persistent ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
   F::fill_async(tw, gtw);
   cp_async_commit();
   if (it < ce) {
