@@ -237,8 +237,9 @@ def main() -> None:
     ap.add_argument("--no-pft-batch", action="store_true")
     ap.add_argument("--pft-frames", type=int, default=4096)
     ap.add_argument("--no-batch64", action="store_true")
-    ap.add_argument("--sweep-launch", choices=["auto", "persistent", "per-colour"], default="auto",
-                    help="coloured sweeps as one cooperative launch or one launch per colour (auto: the "
+    ap.add_argument("--sweep-launch", choices=["auto", "dataflow", "persistent", "per-colour"], default="auto",
+                    help="coloured sweeps as one cooperative launch (per-position waits on overlapping "
+                         "predecessors, or a grid barrier per colour) or one launch per colour (auto: the "
                          "autotuner's choice; with --no-autotune, per colour)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the built-in cluster-size heuristic instead of timing each size (for profilers, "
@@ -294,7 +295,8 @@ def main() -> None:
     ncol = int(ctx.colours().max()) + 1
     if args.sweep_launch != "auto" and mode == pft.MODE_COLOURED:
         for tr in (pft.TRANSFORM_PFT, pft.TRANSFORM_FULL):
-            ctx.set_persistent(tr, args.sweep_launch == "persistent")
+            ctx.set_persistent(tr, {"per-colour": pft.LAUNCH_PER_COLOUR, "persistent": pft.LAUNCH_PERSISTENT,
+                                    "dataflow": pft.LAUNCH_DATAFLOW}[args.sweep_launch])
     tuning = ctx.info()
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -424,7 +426,8 @@ def hbm_peak() -> tuple[float, str]:
 
 def kernel_launches(mode, ncol, tuning, transform):
     """Launches of the fused PIE kernel per sweep: one per colour, or one for the
-    whole sweep when the autotuner kept the cooperative form (and in batched mode)."""
+    whole sweep when the autotuner kept a cooperative form (grid barrier or
+    dataflow), and in batched mode."""
     from paper_2408_03532_gb300 import pft
     if mode != pft.MODE_COLOURED or tuning.get(f"persistent_{transform}"):
         return 1

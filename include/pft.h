@@ -69,6 +69,16 @@ extern "C" {
 #define PIE_MODE_BATCHED     1   /* all positions read the same object; updates
                                     summed and divided by the illumination       */
 
+/* Launch forms of a coloured sweep (pie_ctx_set_persistent); all three give
+ * the same result, bit for bit. */
+#define PIE_LAUNCH_PER_COLOUR 0  /* one launch per colour                        */
+#define PIE_LAUNCH_PERSISTENT 1  /* one cooperative launch, grid barrier between
+                                    colours                                      */
+#define PIE_LAUNCH_DATAFLOW   2  /* one cooperative launch over the colour-major
+                                    schedule; a position waits only for the
+                                    earlier positions whose patches overlap its
+                                    own (no barrier between colours)             */
+
 /* Last error message of the calling thread ("" if none). Never NULL. */
 const char* pft_last_error(void);
 
@@ -217,8 +227,9 @@ typedef struct pie_ctx_info {
   int p, q, r;
   int cluster_pft, cluster_full;
   double sweep_ms_pft, sweep_ms_full;
-  int persistent_pft, persistent_full;  /* 1: coloured sweeps run as one
-                                           cooperative launch per sweep */
+  int persistent_pft, persistent_full;  /* launch form of the coloured sweeps:
+                                           PIE_LAUNCH_* (the dataflow form
+                                           reports its own cluster size above) */
 } pie_ctx_info;
 
 int pie_ctx_info_get(const pie_ctx* ctx, pie_ctx_info* info);
@@ -303,14 +314,23 @@ int pie_tv_step(pie_ctx* ctx, void* object, double lambda, double eps, void* str
  * with that order inside each colour. Synchronises the device. */
 int pie_ctx_set_order(pie_ctx* ctx, const int32_t* order);
 
-/* How coloured sweeps of `transform` are launched: persistent = 1 runs the
- * whole sweep as one cooperative launch (the fused kernel loops over the
- * colours with a grid barrier in between; as many clusters as fit on the GPU
- * at once), 0 one launch per colour. Results are identical either way (the
- * colour order and the per-position arithmetic do not change). The
- * autotuner sets this at creation; UNSUPPORTED in batched mode or when the
- * transform is not built. If the device refuses the cooperative launch, the
- * next sweep falls back to one launch per colour (pie_ctx_info_get shows it). */
+/* How coloured sweeps of `transform` are launched (PIE_LAUNCH_*):
+ * PIE_LAUNCH_PERSISTENT runs the whole sweep as one cooperative launch (the
+ * fused kernel loops over the colours with a grid barrier in between; as many
+ * clusters as fit on the GPU at once); PIE_LAUNCH_DATAFLOW is one cooperative
+ * launch over the colour-major schedule in which each position waits, on
+ * per-position completion counters, only for the earlier positions whose
+ * patches overlap its own (transitively reduced at set-up), so positions of
+ * consecutive colours run at the same time; PIE_LAUNCH_PER_COLOUR is one
+ * launch per colour. Results are identical in all three (every patch is read
+ * after all earlier overlapping positions wrote it and before any later one
+ * does; the per-position arithmetic does not change). Waits are bounded
+ * (2 s): a timeout is latched and returned by the next call as
+ * PFT_ERR_TIMEOUT. The autotuner picks the fastest form (and, for the
+ * dataflow form, its cluster size) at creation; INVALID_ARG for another
+ * value, UNSUPPORTED in batched mode or when the transform is not built. If
+ * the device refuses the cooperative launch, the next sweep falls back to one
+ * launch per colour (pie_ctx_info_get shows it). */
 int pie_ctx_set_persistent(pie_ctx* ctx, int transform, int persistent);
 
 /* Phase-aligned error min_phi ||e^{i phi} z - truth|| / ||truth|| over the

@@ -249,7 +249,16 @@ struct pie_ctx {
   unsigned* d_gbar = nullptr;  // [2]: grid-barrier arrivals, error word
   int* h_gstatus = nullptr;    // mapped host status word of the persistent sweeps
   int* d_gstatus = nullptr;
-  bool persist[2] = {false, false};  // coloured sweeps as one cooperative launch (autotuned)
+  // launch form of the coloured sweeps per transform (autotuned): PIE_LAUNCH_PER_COLOUR,
+  // PIE_LAUNCH_PERSISTENT (one cooperative launch, grid barrier between colours) or
+  // PIE_LAUNCH_DATAFLOW (one cooperative launch, per-item waits on overlapping predecessors)
+  int persist[2] = {PIE_LAUNCH_PER_COLOUR, PIE_LAUNCH_PER_COLOUR};
+  int flow_ci[2] = {-1, -1};   // log2 cluster size of the dataflow form (-1: as the persistent form)
+  int* d_dep_off = nullptr;    // dataflow predecessors per schedule item: CSR offsets [N + 1]
+  int* d_dep = nullptr;        // and schedule indices
+  unsigned* d_done = nullptr;  // [N] CTAs finished per schedule item (zeroed by every sweep)
+  int* d_flow_off = nullptr;   // {0, N}: the whole schedule as one "colour"
+  long long ndep = 0;
   float* d_inv_illum = nullptr;
   unsigned char* d_mask = nullptr;
   float2* d_prev = nullptr;
@@ -360,6 +369,59 @@ int upload_schedule(pie_ctx* c, cudaStream_t st) {
                                cudaMemcpyHostToDevice, st));
   c->max_colour = 0;
   for (int k = 0; k < c->ncol; ++k) c->max_colour = std::max(c->max_colour, c->col_off[k + 1] - c->col_off[k]);
+  // dataflow predecessors: E(s) = the earlier schedule items whose patches
+  // overlap item s (all of an earlier colour). An item b of E(s) that is also in
+  // E(a) for some a of E(s) is dropped: a itself waited for b before it ran, so
+  // waiting for a covers b (by induction along the schedule).
+  const int N = c->npos, n = c->n;
+  std::vector<int> inv(N);
+  for (int s = 0; s < N; ++s) inv[sched[s]] = s;
+  const int cw = (c->W + n - 1) / n + 1, ch = (c->H + n - 1) / n + 1;
+  std::vector<std::vector<int>> cells((size_t)cw * ch);
+  std::vector<std::vector<int>> E(N);
+  for (int s = 0; s < N; ++s) {
+    const int2 p = c->h_pos[sched[s]];
+    const int cx = p.y / n, cy = p.x / n;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int yy = cy + dy, xx = cx + dx;
+        if (yy < 0 || xx < 0 || yy >= ch || xx >= cw) continue;
+        for (int i : cells[(size_t)yy * cw + xx]) {
+          const int2 q = c->h_pos[sched[i]];
+          if (std::abs(q.x - p.x) < n && std::abs(q.y - p.y) < n) E[s].push_back(i);
+        }
+      }
+    cells[(size_t)cy * cw + cx].push_back(s);
+  }
+  std::vector<int> off(N + 1, 0), dep;
+  std::vector<char> mark(N, 0);  // 1: in E(s), 2: covered by another member of E(s)
+  for (int s = 0; s < N; ++s) {
+    for (int b : E[s]) mark[b] = 1;
+    for (int a : E[s])
+      for (int b : E[a])
+        if (mark[b]) mark[b] = 2;
+    for (int b : E[s]) {
+      if (mark[b] == 1) dep.push_back(b);
+      mark[b] = 0;
+    }
+    off[s + 1] = (int)dep.size();
+  }
+  c->ndep = (long long)dep.size();
+  cudaFree(c->d_dep_off);
+  cudaFree(c->d_dep);
+  cudaFree(c->d_done);
+  cudaFree(c->d_flow_off);
+  c->d_dep_off = c->d_dep = c->d_flow_off = nullptr;
+  c->d_done = nullptr;
+  const int flow_off[2] = {0, N};
+  PFT_CUDA_TRY(cudaMalloc(&c->d_dep_off, sizeof(int) * (N + 1)));
+  PFT_CUDA_TRY(cudaMalloc(&c->d_dep, sizeof(int) * std::max<size_t>(1, dep.size())));
+  PFT_CUDA_TRY(cudaMalloc(&c->d_done, sizeof(unsigned) * N));
+  PFT_CUDA_TRY(cudaMalloc(&c->d_flow_off, sizeof(flow_off)));
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_dep_off, off.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st));
+  if (!dep.empty())
+    PFT_CUDA_TRY(cudaMemcpyAsync(c->d_dep, dep.data(), sizeof(int) * dep.size(), cudaMemcpyHostToDevice, st));
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_flow_off, flow_off, sizeof(flow_off), cudaMemcpyHostToDevice, st));
   PFT_CUDA_TRY(cudaStreamSynchronize(st));
   return PFT_OK;
 }
@@ -420,22 +482,35 @@ int persist_ci(const pie_ctx* c, int t) {
   return -1;
 }
 
+// The dataflow form (PIE_LAUNCH_DATAFLOW) runs the same kernel over the whole
+// colour-major schedule as one list, item s going to cluster s mod (clusters):
+// every item waits only for its overlapping predecessors instead of a barrier
+// per colour, so items of consecutive colours overlap in time. The result is
+// the same as the per-colour form's: an item reads its patch after every
+// earlier overlapping item has written it and before any later one does, and
+// items of one colour are disjoint. All clusters are co-resident (cooperative
+// launch) and each runs its items in schedule order, so every wait ends.
 int launch_pie_persistent(pie_ctx* c, int transform, PieArgs a, cudaStream_t st) {
   const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
-  const int ci = persist_ci(c, t);
+  const bool flow = c->persist[t] == PIE_LAUNCH_DATAFLOW;
+  const int ci = (flow && c->flow_ci[t] >= 0) ? c->flow_ci[t] : persist_ci(c, t);
   if (ci < 0) return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for this transform");
   const PieKernel& k = c->kern[t][MODE_COLOURED][ci];
   if (!k.fn) return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for this transform");
-  const long long clusters =
-      std::max<long long>(1, std::min<long long>(c->max_colour, c->cap[t][MODE_COLOURED][ci] / k.cluster));
+  const long long clusters = std::max<long long>(
+      1, std::min<long long>(flow ? c->npos : c->max_colour, c->cap[t][MODE_COLOURED][ci] / k.cluster));
   a.list = c->d_sched;
   a.count = 0;
-  a.col_off = c->d_coloff;
-  a.ncol = c->ncol;
+  a.col_off = flow ? c->d_flow_off : c->d_coloff;
+  a.ncol = flow ? 1 : c->ncol;
   a.gbar = c->d_gbar;
   a.gerr = reinterpret_cast<int*>(c->d_gbar + 1);
   a.gstatus = c->d_gstatus;
+  a.dep_off = flow ? c->d_dep_off : nullptr;
+  a.dep = flow ? c->d_dep : nullptr;
+  a.done = flow ? c->d_done : nullptr;
   PFT_CUDA_TRY(cudaMemsetAsync(c->d_gbar, 0, 2 * sizeof(unsigned), st));
+  if (flow) PFT_CUDA_TRY(cudaMemsetAsync(c->d_done, 0, sizeof(unsigned) * c->npos, st));
   PftConst cst = c->plan.cst;
   const float2* W = c->plan.d_W;
   const float2* tw = t == 0 ? c->plan.d_twp : pfth::twiddles(c->n);
@@ -502,27 +577,49 @@ int autotune(pie_ctx* c, cudaStream_t st) {
     }
     c->tuned[t][mode] = best;
     c->tuned_ms[t] = best >= 0 ? best_ms / 2.0 : 0.0;
-    // coloured sweeps: the same kernel as one cooperative launch per sweep
+    // coloured sweeps: the same kernel as one cooperative launch per sweep, with
+    // a grid barrier per colour (at the tuned cluster size) or with per-item
+    // waits (every built cluster size); the fastest form is kept
     if (rc == PFT_OK && best >= 0 && mode == MODE_COLOURED && c->d_gbar) {
-      c->persist[t] = true;
-      k_fill<<<grid_for(HW), kThreads, 0, st>>>(scratch, HW, make_float2(0.7f, 0.2f));
-      int prc = enqueue_sweep(c, scratch, tr, 1.0, false, st);
-      if (prc == PFT_OK) {
-        cudaEventRecord(e0, st);
-        for (int rep = 0; rep < 2 && prc == PFT_OK; ++rep) prc = enqueue_sweep(c, scratch, tr, 1.0, false, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) prc = PFT_ERR_CUDA;
+      auto try_form = [&](int form, int fci) {
+        c->persist[t] = form;
+        c->flow_ci[t] = fci;
+        k_fill<<<grid_for(HW), kThreads, 0, st>>>(scratch, HW, make_float2(0.7f, 0.2f));
+        int prc = enqueue_sweep(c, scratch, tr, 1.0, false, st);
+        if (prc == PFT_OK) {
+          cudaEventRecord(e0, st);
+          for (int rep = 0; rep < 2 && prc == PFT_OK; ++rep) prc = enqueue_sweep(c, scratch, tr, 1.0, false, st);
+          cudaEventRecord(e1, st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) prc = PFT_ERR_CUDA;
+        }
+        float ms = 0.f;
+        if (prc == PFT_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (prc != PFT_OK || *c->h_gstatus != PFT_OK) {
+          *c->h_gstatus = PFT_OK;
+          cudaGetLastError();  // a refused cooperative launch is not sticky
+          if (cudaStreamSynchronize(st) != cudaSuccess) rc = pfth::set_error(PFT_ERR_CUDA, "autotune sweep failed");
+          return 1e30f;
+        }
+        return ms;
+      };
+      int best_form = PIE_LAUNCH_PER_COLOUR, best_fci = -1;
+      float ms = try_form(PIE_LAUNCH_PERSISTENT, -1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_form = PIE_LAUNCH_PERSISTENT;
       }
-      float ms = 0.f;
-      if (prc == PFT_OK) cudaEventElapsedTime(&ms, e0, e1);
-      if (prc != PFT_OK || *c->h_gstatus != PFT_OK || !(ms < best_ms)) {
-        c->persist[t] = false;
-        *c->h_gstatus = PFT_OK;
-        cudaGetLastError();  // a refused cooperative launch is not sticky
-        if (cudaStreamSynchronize(st) != cudaSuccess) rc = pfth::set_error(PFT_ERR_CUDA, "autotune sweep failed");
-      } else {
-        c->tuned_ms[t] = ms / 2.0;
+      for (int q = 0; q < 4 && rc == PFT_OK && c->d_done; ++q) {
+        if (!c->kern[t][mode][q].fn) continue;
+        ms = try_form(PIE_LAUNCH_DATAFLOW, q);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_form = PIE_LAUNCH_DATAFLOW;
+          best_fci = q;
+        }
       }
+      c->persist[t] = best_form;
+      c->flow_ci[t] = best_fci;
+      c->tuned_ms[t] = best_ms / 2.0;
     }
   }
   cudaEventDestroy(e0);
@@ -547,6 +644,10 @@ int pie_ctx_destroy(pie_ctx* c) {
   cudaFree(c->d_ampc);
   cudaFree(c->d_sched);
   cudaFree(c->d_coloff);
+  cudaFree(c->d_dep_off);
+  cudaFree(c->d_dep);
+  cudaFree(c->d_done);
+  cudaFree(c->d_flow_off);
   cudaFree(c->d_gbar);
   if (c->h_gstatus) cudaFreeHost(c->h_gstatus);
   cudaFree(c->d_inv_illum);
@@ -702,8 +803,12 @@ int pie_ctx_info_get(const pie_ctx* c, pie_ctx_info* info) {
   info->cluster_full = c->tuned[1][mode] >= 0 ? (1 << c->tuned[1][mode]) : 0;
   info->sweep_ms_pft = c->tuned_ms[0];
   info->sweep_ms_full = c->tuned_ms[1];
-  info->persistent_pft = c->persist[0] ? 1 : 0;
-  info->persistent_full = c->persist[1] ? 1 : 0;
+  info->persistent_pft = c->persist[0];
+  info->persistent_full = c->persist[1];
+  for (int t = 0; t < 2; ++t) {  // the dataflow form may run another cluster size
+    if (c->persist[t] != PIE_LAUNCH_DATAFLOW || c->flow_ci[t] < 0) continue;
+    (t == 0 ? info->cluster_pft : info->cluster_full) = 1 << c->flow_ci[t];
+  }
   return PFT_OK;
 }
 
@@ -815,7 +920,7 @@ int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats,
     // a cooperative launch that cannot be captured: per-colour launches instead
     if (attempt == 0 && c->persist[t] && gamma < 0.0 && mode == PIE_MODE_COLOURED) {
       cudaGetLastError();
-      c->persist[t] = false;
+      c->persist[t] = PIE_LAUNCH_PER_COLOUR;
       continue;
     }
     if (rc != PFT_OK) return rc;
@@ -936,11 +1041,13 @@ int pie_ctx_set_persistent(pie_ctx* c, int transform, int persistent) {
   if (c->pb.mode != PIE_MODE_COLOURED)
     return pfth::set_error(PFT_ERR_UNSUPPORTED, "persistent sweeps are built for coloured mode");
   if (t == 1 && !c->have_full) return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is not built for this n");
+  if (persistent < PIE_LAUNCH_PER_COLOUR || persistent > PIE_LAUNCH_DATAFLOW)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown launch form %d", persistent);
   if (persistent && persist_ci(c, t) < 0)
     return pfth::set_error(PFT_ERR_UNSUPPORTED, "no kernel for a persistent sweep");
-  if (c->persist[t] != (persistent != 0)) {
+  if (c->persist[t] != persistent) {
     PFT_CUDA_TRY(cudaDeviceSynchronize());
-    c->persist[t] = persistent != 0;
+    c->persist[t] = persistent;
     for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
     c->graphs.clear();
   }

@@ -71,6 +71,14 @@ struct PieArgs {
   unsigned* gbar;           // arrival counter, zero at launch
   int* gerr;                // set when a barrier gives up (device word, zero at launch)
   int* gstatus;             // mapped host status word: PFT_ERR_TIMEOUT on a timeout
+  // dataflow sweep (dep_off != nullptr, persistent with one "colour" holding the
+  // whole colour-major schedule): item s waits until done[d] == C for every
+  // predecessor d in dep[dep_off[s] .. dep_off[s + 1]) (the earlier items whose
+  // patches overlap its own, transitively reduced), and each of its C CTAs adds
+  // one to done[s] once its part of the update is written
+  const int* dep_off;
+  const int* dep;
+  unsigned* done;           // [schedule length], zero at launch
 };
 
 template <int C>
@@ -145,6 +153,56 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Dataflow sweep: before reading its patch, schedule item s waits until every
+// predecessor has been written by all C CTAs of the cluster that ran it. Warp 0
+// polls, one predecessor per lane, with acquire loads; each wait is bounded at
+// 2 s. A wait that gives up (or finds that another CTA gave up) sets the error
+// words and returns without waiting: the CTA still runs every item and cluster
+// barrier of its list, so the launch ends, and the host reports the timeout.
+template <int C>
+__device__ __forceinline__ void wait_deps(const PieArgs& a, int s) {
+  if (threadIdx.x < 32) {
+    const int b = a.dep_off[s], e = a.dep_off[s + 1];
+    bool ok = *reinterpret_cast<volatile int*>(a.gerr) == 0;
+    for (int i = b + (int)threadIdx.x; ok && i < e; i += 32) {
+      const unsigned* f = a.done + a.dep[i];
+      unsigned long long t0, t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      while (true) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+        if (v >= (unsigned)C) break;
+        if (*reinterpret_cast<volatile int*>(a.gerr)) {
+          ok = false;
+          break;
+        }
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 2000000000ull) {
+          atomicExch(a.gerr, 1);
+          if (a.gstatus) {
+            *reinterpret_cast<volatile int*>(a.gstatus) = PFT_ERR_TIMEOUT;
+            __threadfence_system();
+          }
+          ok = false;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Dataflow sweep: this CTA's part of item s's update is written (every thread's
+// stores ordered before the release by the barrier and the fence).
+__device__ __forceinline__ void signal_done(const PieArgs& a, int s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(a.done + s, 1u);
+  }
 }
 
 // Modulus-projection residual (Eq. 3) and its contribution to the objective.
@@ -367,6 +425,7 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
   };
   const int step = gridDim.x / C;
   const bool persistent = MODE == MODE_COLOURED && a.ncol > 0;  // every colour in this launch
+  const bool flow = persistent && a.dep_off != nullptr;         // per-item waits instead
   const int ncol = persistent ? a.ncol : 1;
   int ce = persistent ? a.col_off[1] : a.count;
   int it = (persistent ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
@@ -376,6 +435,7 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
   if (it < ce) {
     const PieItem q = resolve<M * M>(a, it);
     gather_static(q);
+    if (flow) wait_deps<C>(a, it);
     gather_obj(q);
   } else {
     cp_async_commit();
@@ -468,9 +528,11 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
     }
     if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
     }  // round
+    if (flow) signal_done(a, it);
     if (it + step < ce) {  // the next item of this colour
       const PieItem q = resolve<M * M>(a, it + step);
       gather_static(q);
+      if (flow) wait_deps<C>(a, it + step);
       gather_obj(q);
     }
     if constexpr (C == 1) __syncthreads();
@@ -542,6 +604,7 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
   };
   const int step = gridDim.x / C;
   const bool persistent = MODE == MODE_COLOURED && a.ncol > 0;  // every colour in this launch
+  const bool flow = persistent && a.dep_off != nullptr;         // per-item waits instead
   const int ncol = persistent ? a.ncol : 1;
   int ce = persistent ? a.col_off[1] : a.count;
   int it = (persistent ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
@@ -550,6 +613,7 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
   if (it < ce) {
     const PieItem q = resolve<N * N>(a, it);
     gather_static(q);
+    if (flow) wait_deps<C>(a, it);
     gather_obj(q);
   } else {
     cp_async_commit();
@@ -650,9 +714,11 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
     }
     if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
     }  // round
+    if (flow) signal_done(a, it);
     if (it + step < ce) {  // the next item of this colour
       const PieItem q = resolve<N * N>(a, it + step);
       gather_static(q);
+      if (flow) wait_deps<C>(a, it + step);
       gather_obj(q);
     }
     if constexpr (C == 1) __syncthreads();

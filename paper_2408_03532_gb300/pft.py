@@ -24,6 +24,7 @@ PREC_FP32 = 0
 PREC_SPLIT_BF16 = 1
 TRANSFORM_PFT, TRANSFORM_FULL = 0, 1
 MODE_COLOURED, MODE_BATCHED = 0, 1
+LAUNCH_PER_COLOUR, LAUNCH_PERSISTENT, LAUNCH_DATAFLOW = 0, 1, 2
 _ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "OOM"}
 
 
@@ -347,9 +348,13 @@ class PieContext:
             raise ValueError("order must be a permutation of the positions")
         _check(load().pie_ctx_set_order(self._h, o.ctypes.data))
 
-    def set_persistent(self, transform: int, persistent: bool = True):
-        """Coloured sweeps of `transform` as one cooperative launch (True) or one launch per colour."""
-        _check(load().pie_ctx_set_persistent(self._h, transform, 1 if persistent else 0))
+    def set_persistent(self, transform: int, persistent=True):
+        """Launch form of the coloured sweeps of `transform`: LAUNCH_PER_COLOUR
+        (or False), LAUNCH_PERSISTENT (or True: one cooperative launch, grid
+        barrier between colours) or LAUNCH_DATAFLOW (one cooperative launch,
+        per-position waits on overlapping predecessors)."""
+        form = int(persistent) if not isinstance(persistent, bool) else (1 if persistent else 0)
+        _check(load().pie_ctx_set_persistent(self._h, transform, form))
 
     def iteration_blind(self, obj, transform: int = TRANSFORM_FULL, beta: float = 1.0, gamma: float = 1.0,
                         stats: bool = True, stream=None):

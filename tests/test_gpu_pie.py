@@ -94,22 +94,25 @@ def test_coloured_sweep_matches_oracle(env, small, mid, transform, which):
     assert st["rel_change"] == pytest.approx(opie.relative_change(zo, P["init"]), rel=1e-4)
 
 
+@pytest.mark.parametrize("form", ["persistent", "dataflow"])
 @pytest.mark.parametrize("transform", ["pft", "full"])
 @pytest.mark.parametrize("which", ["mid", "wide"])
-def test_persistent_sweep_matches_per_colour_launches(env, mid, wide_colours, transform, which):
-    """A coloured sweep as one cooperative launch (grid barrier between colours)
-    gives the same object, bit for bit, as one launch per colour."""
+def test_persistent_sweep_matches_per_colour_launches(env, mid, wide_colours, transform, which, form):
+    """A coloured sweep as one cooperative launch (grid barrier between colours,
+    or per-position waits on the overlapping predecessors) gives the same
+    object, bit for bit, as one launch per colour."""
     torch, pft = env
     P = mid if which == "mid" else wide_colours
     tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    f = pft.LAUNCH_PERSISTENT if form == "persistent" else pft.LAUNCH_DATAFLOW
     a, b = make_ctx(P, torch, pft), make_ctx(P, torch, pft)
-    a.set_persistent(tr, False)
-    b.set_persistent(tr, True)
+    a.set_persistent(tr, pft.LAUNCH_PER_COLOUR)
+    b.set_persistent(tr, f)
     za, zb = c64(P["init"], torch), c64(P["init"], torch)
     for _ in range(2):
         sa = a.iteration(za, tr, 0.9)
         sb = b.iteration(zb, tr, 0.9)
-    assert b.info()[f"persistent_{transform}"] == 1
+    assert b.info()[f"persistent_{transform}"] == f
     assert a.info()[f"persistent_{transform}"] == 0
     assert torch.equal(za, zb)
     assert sb["phi"] == pytest.approx(sa["phi"], rel=1e-6)
@@ -264,6 +267,32 @@ def test_full_size_sweep_noise_free(env, full_size_clean, transform):
     zo, phi = opie.pie_sweep(start.astype(np.complex128), P["probe"], P["pos"], d, T, 1.0, order)
     assert rel(z.cpu().numpy(), zo) < TOL
     assert st["phi"] == pytest.approx(phi, rel=1e-4)
+
+
+@pytest.mark.parametrize("transform", ["pft", "full"])
+def test_dataflow_sweep_at_full_size_and_in_random_order(env, full_size, transform):
+    """The dataflow launch form on the 1024^2 / 128^2 / 3600-position problem
+    gives the per-colour launches' object bit for bit, over two sweeps, before
+    and after a re-colouring in a random visiting order (which rebuilds the
+    predecessor lists)."""
+    torch, pft = env
+    P = full_size
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    a, b = make_ctx(P, torch, pft), make_ctx(P, torch, pft)
+    a.set_persistent(tr, pft.LAUNCH_PER_COLOUR)
+    b.set_persistent(tr, pft.LAUNCH_DATAFLOW)
+    for order in (None, np.random.default_rng(5).permutation(len(P["pos"])).astype(np.int32)):
+        if order is not None:
+            a.set_order(order)
+            b.set_order(order)
+            assert np.array_equal(a.colours(), b.colours())
+        za, zb = c64(P["init"], torch), c64(P["init"], torch)
+        for _ in range(2):
+            sa = a.iteration(za, tr, 1.0)
+            sb = b.iteration(zb, tr, 1.0)
+        assert b.info()[f"persistent_{transform}"] == pft.LAUNCH_DATAFLOW
+        assert torch.equal(za, zb)
+        assert sb["phi"] == pytest.approx(sa["phi"], rel=1e-6)
 
 
 @pytest.mark.parametrize("transform", ["pft", "full"])
