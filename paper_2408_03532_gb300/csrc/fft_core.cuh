@@ -1,6 +1,6 @@
-// N-point FFTs on one warp (N = L * E, L = min(N, 32) lanes, E per lane), the
-// building block of the full 2-D transform used by the refine phase of the
-// hybrid (Algorithm 3, step 3) and by the FFT-then-crop baseline.
+// N-point FFTs on one warp (N = L * E: L lanes, min(N, 32) by default, E values
+// per lane), the building block of the full 2-D transform used by the refine
+// phase of the hybrid (Algorithm 3, step 3) and by the FFT-then-crop baseline.
 //
 // A row held as x[e] = v[lane + L e] is transformed in three steps:
 //   1. an E-point DFT over e in registers,
@@ -15,9 +15,10 @@
 
 namespace pftk {
 
-template <int N>
+template <int N, int LANES = (N < 32 ? N : 32)>
 struct Fft {
-  static constexpr int L = N < 32 ? N : 32;
+  static_assert(LANES >= 2 && LANES <= 32 && N % LANES == 0, "lanes per row");
+  static constexpr int L = LANES;
   static constexpr int E = N / L;
   static constexpr int G = 32 / L;  // rows per warp
   static constexpr int S = N + 1;   // shared row stride (odd: column access conflict-free)

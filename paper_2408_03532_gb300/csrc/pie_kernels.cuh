@@ -549,9 +549,23 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
 }
 
 // ------------------------------------------------------------ FFT variant
-template <int N, int C>
+// Lanes per row of the full-FFT kernel: the default split (min(N, 32) lanes)
+// unless fewer lanes with at most 8 values each let every warp own exactly one
+// row group of the CTA's N / C rows (then the probe and patch values stay in
+// registers from the exit wave to the update, and each phase is one pass).
+template <int N, int C, int NT>
+constexpr int pie_full_lanes() {
+  const int L0 = N < 32 ? N : 32, NW = NT / 32, RN = N / C;
+  if (RN < NW || RN % NW != 0) return L0;
+  const int G = RN / NW;
+  if (32 % G != 0) return L0;
+  const int L = 32 / G;
+  return (L <= L0 && L >= 2 && N % L == 0 && N / L <= 8) ? L : L0;
+}
+
+template <int N, int C, int NT = 256>
 struct PieFullShape {
-  using F = Fft<N>;
+  using F = Fft<N, pie_full_lanes<N, C, NT>()>;
   static constexpr int RN = N / C, CN = N / C;
   static constexpr bool VALID = (N % C == 0) && RN >= 1 && (RN % F::G == 0) && (CN % F::G == 0);
   static constexpr int SCS = CN + 1;  // column slice: [N][CN + 1]
@@ -566,8 +580,8 @@ struct PieFullShape {
 
 template <int N, int MODE, int C, int NT>
 __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(PieArgs a, const float2* __restrict__ gtw) {
-  using S = PieFullShape<N, C>;
-  using F = Fft<N>;
+  using S = PieFullShape<N, C, NT>;
+  using F = typename S::F;
   using CL = Cluster<C>;
   constexpr int L = F::L, E = F::E, G = F::G, RN = S::RN, CN = S::CN, NW = NT / 32;
   extern __shared__ __align__(16) float2 sm[];
