@@ -611,7 +611,8 @@ def measure_batch64(pft, synth, torch, dev, stream, flush, reps: int = 3) -> dic
     """64 independent reconstructions of different sizes (objects 256^2-2048^2,
     probes 64^2-256^2, 50-2000 Fermat positions, M in {16, 32, 64}) swept
     together: one PFT sweep over all instances per graph launch, coloured
-    (exact PIE order) and batched modes, timed with CUDA events."""
+    (exact PIE order: one launch per class and colour, and one dataflow
+    launch per shape class) and batched modes, timed with CUDA events."""
     specs = synth.uneven_batch_recipe(64)
     insts, inits = [], []
     for sp in specs:
@@ -623,8 +624,12 @@ def measure_batch64(pft, synth, torch, dev, stream, flush, reps: int = 3) -> dic
         inits.append(torch.from_numpy(inst["init"].astype(np.complex64)).to(dev))
     frames = sum(sp["npos"] for sp in specs)
     out = {"instances": len(specs), "positions": frames}
-    for name, mode in (("coloured", pft.MODE_COLOURED), ("batched", pft.MODE_BATCHED)):
+    for name, mode, form in (("coloured", pft.MODE_COLOURED, pft.LAUNCH_PER_COLOUR),
+                             ("coloured_dataflow", pft.MODE_COLOURED, pft.LAUNCH_DATAFLOW),
+                             ("batched", pft.MODE_BATCHED, None)):
         B = pft.PieBatch(insts, mode=mode)
+        if form is not None:
+            B.set_launch(form)
         objs = [z.clone() for z in inits]
         B.iteration(objs, pft.TRANSFORM_PFT, 1.0, stats=False)
         ms = []

@@ -353,9 +353,14 @@ int pie_amp_loss_grad(pie_ctx* ctx, const void* object, const void* probe, void*
  * object, probe, scan and output size of each instance are its own). One call
  * sweeps every position of every instance: instances with the same (n, M) form
  * a shape class whose positions share one kernel launch per colour (coloured
- * mode: launch c runs colour c of all of them) or one launch per sweep
- * (batched mode); the classes run as parallel branches of one CUDA graph,
- * captured on first use and replayed.
+ * mode in the default PIE_LAUNCH_PER_COLOUR form: launch c runs colour c of all
+ * of them) or one launch per sweep (batched mode, and coloured mode in the
+ * PIE_LAUNCH_DATAFLOW form: the class's colour-major work list in one launch,
+ * each position waiting only for the earlier positions of its own instance
+ * whose patches overlap its own, with clusters claiming positions in list
+ * order so that the classes' launches can share the GPU in any proportion).
+ * The two coloured forms give the same objects. The classes run as parallel
+ * branches of one CUDA graph, captured on first use and replayed.
  *
  * pie_batch_create(out, count, problems, probes, positions, intensities, stream)
  *   problems: host [count] (all with the same mode; `autotune` is ignored);
@@ -366,6 +371,10 @@ int pie_amp_loss_grad(pie_ctx* ctx, const void* object, const void* probe, void*
  *   phi: host double [count] or NULL; with it the call synchronises and
  *   writes each instance's Phi (as pie_stats.phi).
  * pie_batch_classes: number of shape classes and kernel launches per sweep.
+ * pie_batch_set_launch(b, form): PIE_LAUNCH_PER_COLOUR (default) or
+ *   PIE_LAUNCH_DATAFLOW for a coloured batch (INVALID_ARG for another form,
+ *   UNSUPPORTED for a batched-mode batch); synchronises the device. A wait that
+ *   gives up (2 s) is returned as PFT_ERR_TIMEOUT by the call that sees it.
  */
 typedef struct pie_batch pie_batch;
 
@@ -375,6 +384,7 @@ int pie_batch_destroy(pie_batch* batch);
 int pie_batch_iteration(pie_batch* batch, void* const* objects, int transform, double beta, double* phi,
                         void* stream);
 int pie_batch_classes(const pie_batch* batch, int* nclasses, int* launches_per_sweep);
+int pie_batch_set_launch(pie_batch* batch, int form);
 
 /* ---- allocation-free error reduction ------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot

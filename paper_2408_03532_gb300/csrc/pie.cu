@@ -233,6 +233,10 @@ struct pie_ctx {
   // kernels per [transform][mode][log2 cluster size] with their resident-CTA capacity
   PieKernel kern[2][3][4];
   long long cap[2][3][4] = {};
+  // per transform: the item-claiming coloured kernel with the most CTAs per
+  // position that is built (batch dataflow sweeps), and its capacity
+  PieKernel kern_claim[2];
+  long long cap_claim[2] = {0, 0};
   int tuned[2][3] = {{-1, -1, -1}, {-1, -1, -1}};  // autotuned log2 cluster size, -1 = heuristic
   double tuned_ms[2] = {0.0, 0.0};                  // sweep time of the chosen variant
   float2* d_probe = nullptr;
@@ -258,7 +262,8 @@ struct pie_ctx {
   int* d_dep = nullptr;        // and schedule indices
   unsigned* d_done = nullptr;  // [N] CTAs finished per schedule item (zeroed by every sweep)
   int* d_flow_off = nullptr;   // {0, N}: the whole schedule as one "colour"
-  long long ndep = 0;
+  std::vector<int> h_dep_off, h_dep;  // host copies (batches remap them to their work lists)
+  std::vector<int> h_sched;            // colour-major schedule (host copy)
   float* d_inv_illum = nullptr;
   unsigned char* d_mask = nullptr;
   float2* d_prev = nullptr;
@@ -406,7 +411,9 @@ int upload_schedule(pie_ctx* c, cudaStream_t st) {
     }
     off[s + 1] = (int)dep.size();
   }
-  c->ndep = (long long)dep.size();
+  c->h_dep_off = off;
+  c->h_dep = dep;
+  c->h_sched = sched;
   cudaFree(c->d_dep_off);
   cudaFree(c->d_dep);
   cudaFree(c->d_done);
@@ -736,6 +743,20 @@ int pie_ctx_create(pie_ctx** out, const pie_problem* pb, const void* probe, cons
     if (!any) {
       pie_ctx_destroy(c);
       return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for n=%d M=%d", n, M);
+    }
+    for (int q = 3; q >= 2 && !c->kern_claim[0].fn; --q) {
+      PieKernel k = pfth::pie_pft_kernel(P, Q, MP, MODE_COLOURED, 1 << q, true);
+      if (k.fn) {
+        PIE_TRY(prepare_kernel(k, &c->cap_claim[0]));
+        c->kern_claim[0] = k;
+      }
+    }
+    for (int q = 3; q >= 2 && c->have_full && !c->kern_claim[1].fn; --q) {
+      PieKernel f = pfth::pie_full_kernel(n, MODE_COLOURED, 1 << q, true);
+      if (f.fn) {
+        PIE_TRY(prepare_kernel(f, &c->cap_claim[1]));
+        c->kern_claim[1] = f;
+      }
     }
   }
   if (c->have_full && !pfth::twiddles(n)) {
@@ -1191,8 +1212,20 @@ struct pie_batch {
     std::vector<int> col_off;       // work-list offsets per colour (coloured mode)
     int2* d_work = nullptr;         // (instance, position) pairs, colour-major
     bool have_full = true;
+    // dataflow form (coloured mode): the whole work list in one launch, each
+    // item waiting for its instance's overlapping predecessors
+    int* d_dep_off = nullptr;       // [items + 1]
+    int* d_dep = nullptr;           // work-list indices
+    unsigned* d_done = nullptr;     // [items]
+    unsigned* d_ticket = nullptr;   // [2]: claim counter, error word
+    int* d_flow_off = nullptr;      // {0, items}
+    int max_width = 0;              // items in the class's largest colour
+    int chain = 1;                  // longest dependency chain: the members' largest colour count
   };
   std::vector<Class> classes;
+  // coloured mode: PIE_LAUNCH_PER_COLOUR (measured faster on the 64-instance
+  // recipe: 119 ms against 166 ms per PFT sweep) or PIE_LAUNCH_DATAFLOW
+  int launch = PIE_LAUNCH_PER_COLOUR;
   std::vector<PieInstance> h_inst;
   double* d_red = nullptr;
   double* h_red = nullptr;
@@ -1232,6 +1265,37 @@ void batch_descriptors(pie_batch* b, void* const* objects, int transform, double
   }
 }
 
+// One dataflow launch over a shape class's work list: clusters claim items in
+// schedule order (PieArgs::ticket), so the classes' launches may share the GPU
+// in any proportion (no co-residency is needed for the waits to end). `width`
+// clusters at most, capped by what fits on the GPU.
+int launch_pie_claimed(pie_ctx* c, int transform, PieArgs a, int width, cudaStream_t st) {
+  const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
+  const PieKernel& k = c->kern_claim[t];
+  if (!k.fn) return pfth::set_error(PFT_ERR_UNSUPPORTED, "no item-claiming PIE kernel for this transform");
+  const long long clusters = std::max<long long>(1, std::min<long long>(width, c->cap_claim[t] / k.cluster));
+  PftConst cst = c->plan.cst;
+  const float2* W = c->plan.d_W;
+  const float2* tw = t == 0 ? c->plan.d_twp : pfth::twiddles(c->n);
+  if (!tw) return PFT_ERR_CUDA;
+  void* args_pft[] = {(void*)&a, (void*)&cst, (void*)&W, (void*)&tw};
+  void* args_full[] = {(void*)&a, (void*)&tw};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * k.cluster));
+  cfg.blockDim = dim3(k.threads);
+  cfg.dynamicSmemBytes = k.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = k.cluster;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = k.cluster > 1 ? 1 : 0;
+  PFT_CUDA_TRY(cudaLaunchKernelExC(&cfg, k.fn, t == 0 ? args_pft : args_full));
+  return PFT_OK;
+}
+
 int batch_enqueue(pie_batch* b, const PieInstance* d_inst, void* const* objects, int transform, double beta,
                   bool stats, cudaStream_t st) {
   const int mode = b->mode == PIE_MODE_COLOURED ? MODE_COLOURED : MODE_BATCHED;
@@ -1246,7 +1310,35 @@ int batch_enqueue(pie_batch* b, const PieInstance* d_inst, void* const* objects,
     PFT_CUDA_TRY(cudaStreamWaitEvent(bs, b->events[0], 0));
     PieArgs a = {};
     a.inst = d_inst;
-    const int ncol = mode == MODE_COLOURED ? (int)cl.col_off.size() - 1 : 1;
+    pie_ctx* rep = b->ctx[cl.rep];
+    const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
+    const bool flow = mode == MODE_COLOURED && b->launch == PIE_LAUNCH_DATAFLOW && rep->kern_claim[t].fn;
+    if (flow) {
+      const int items = cl.col_off.back();
+      PFT_CUDA_TRY(cudaMemsetAsync(cl.d_done, 0, sizeof(unsigned) * std::max(1, items), bs));
+      PFT_CUDA_TRY(cudaMemsetAsync(cl.d_ticket, 0, 2 * sizeof(unsigned), bs));
+      a.work = cl.d_work;
+      a.count = 0;
+      a.col_off = cl.d_flow_off;
+      a.ncol = 1;
+      a.gbar = cl.d_ticket;
+      a.gerr = reinterpret_cast<int*>(cl.d_ticket + 1);
+      a.gstatus = rep->d_gstatus;
+      a.dep_off = cl.d_dep_off;
+      a.dep = cl.d_dep;
+      a.done = cl.d_done;
+      a.ticket = cl.d_ticket;
+      if (items > 0) {
+        // about twice the class's average parallelism (items over the longest
+        // chain): a class bound by one long chain holds a few clusters, not the
+        // GPU, while its persistent clusters wait
+        const long long par = (2LL * items + cl.chain - 1) / cl.chain;
+        const int width = (int)std::min<long long>(cl.max_width, std::max<long long>(1, par));
+        int rc = launch_pie_claimed(rep, transform, a, width, bs);
+        if (rc != PFT_OK) return rc;
+      }
+    }
+    const int ncol = mode != MODE_COLOURED ? 1 : flow ? 0 : (int)cl.col_off.size() - 1;
     for (int col = 0; col < ncol; ++col) {
       const int off = mode == MODE_COLOURED ? cl.col_off[col] : 0;
       a.work = cl.d_work + off;
@@ -1280,7 +1372,14 @@ int pie_batch_destroy(pie_batch* b) {
     cudaGraphExecDestroy(g.exec);
     cudaFree(g.d_inst);
   }
-  for (auto& cl : b->classes) cudaFree(cl.d_work);
+  for (auto& cl : b->classes) {
+    cudaFree(cl.d_work);
+    cudaFree(cl.d_dep_off);
+    cudaFree(cl.d_dep);
+    cudaFree(cl.d_done);
+    cudaFree(cl.d_ticket);
+    cudaFree(cl.d_flow_off);
+  }
   for (auto* c : b->ctx) pie_ctx_destroy(c);
   cudaFree(b->d_red);
   if (b->h_red) cudaFreeHost(b->h_red);
@@ -1355,6 +1454,42 @@ int pie_batch_create(pie_batch** out, int count, const pie_problem* problems, co
     if (e != cudaSuccess) return fail(e, "cudaMalloc(work)");
     e = cudaMemcpy(cl.d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(e, "cudaMemcpy(work)");
+    if (b->mode != PIE_MODE_COLOURED) continue;
+    // dataflow predecessors: instance i's k-th item in the work list is item k
+    // of its own colour-major schedule, so its predecessor lists carry over
+    const int items = (int)work.size();
+    for (size_t q = 0; q + 1 < cl.col_off.size(); ++q)
+      cl.max_width = std::max(cl.max_width, cl.col_off[q + 1] - cl.col_off[q]);
+    for (int i : cl.members) cl.chain = std::max(cl.chain, b->ctx[i]->ncol);
+    std::vector<std::vector<int>> widx(count);
+    for (int w = 0; w < items; ++w) {
+      const int i = work[w].x;
+      const int k = (int)widx[i].size();
+      if (b->ctx[i]->h_sched[k] != work[w].y) {
+        pie_batch_destroy(b);
+        return pfth::set_error(PFT_ERR_CUDA, "internal: batch work list out of schedule order");
+      }
+      widx[i].push_back(w);
+    }
+    std::vector<int> off(items + 1, 0), dep;
+    for (int w = 0; w < items; ++w) {
+      const int i = work[w].x;
+      const pie_ctx* c = b->ctx[i];
+      const int k = (int)(std::lower_bound(widx[i].begin(), widx[i].end(), w) - widx[i].begin());
+      for (int d = c->h_dep_off[k]; d < c->h_dep_off[k + 1]; ++d) dep.push_back(widx[i][c->h_dep[d]]);
+      off[w + 1] = (int)dep.size();
+    }
+    const int flow_off[2] = {0, items};
+    e = cudaMalloc(&cl.d_dep_off, sizeof(int) * (items + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&cl.d_dep, sizeof(int) * std::max<size_t>(1, dep.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&cl.d_done, sizeof(unsigned) * std::max(1, items));
+    if (e == cudaSuccess) e = cudaMalloc(&cl.d_ticket, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&cl.d_flow_off, sizeof(flow_off));
+    if (e == cudaSuccess) e = cudaMemcpy(cl.d_dep_off, off.data(), sizeof(int) * (items + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !dep.empty())
+      e = cudaMemcpy(cl.d_dep, dep.data(), sizeof(int) * dep.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cl.d_flow_off, flow_off, sizeof(flow_off), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(e, "batch dataflow lists");
   }
   cudaError_t e = cudaMalloc(&b->d_red, sizeof(double) * count);
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_red, sizeof(double) * count);
@@ -1386,6 +1521,15 @@ int pie_batch_iteration(pie_batch* b, void* const* objects, int transform, doubl
       if (!cl.have_full)
         return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n <= 128, not %d",
                                b->ctx[cl.rep]->n);
+  for (auto& cl : b->classes) {  // a wait of an earlier dataflow sweep that gave up
+    pie_ctx* rep = b->ctx[cl.rep];
+    if (rep->h_gstatus && *rep->h_gstatus != PFT_OK) {
+      const int e = *rep->h_gstatus;
+      *rep->h_gstatus = PFT_OK;
+      return pfth::set_error(e, e == PFT_ERR_TIMEOUT ? "a wait of an earlier batch sweep timed out"
+                                                     : "an earlier batch sweep's kernel ran without its cluster shape");
+    }
+  }
   std::vector<void*> objs(objects, objects + b->count);
   cudaGraphExec_t exec = nullptr;
   for (auto& g : b->graphs)
@@ -1425,6 +1569,15 @@ int pie_batch_iteration(pie_batch* b, void* const* objects, int transform, doubl
   PFT_CUDA_TRY(cudaGraphLaunch(exec, st));
   if (phi) {
     PFT_CUDA_TRY(cudaStreamSynchronize(st));
+    for (auto& cl : b->classes) {
+      pie_ctx* rep = b->ctx[cl.rep];
+      if (rep->h_gstatus && *rep->h_gstatus != PFT_OK) {
+        const int e = *rep->h_gstatus;
+        *rep->h_gstatus = PFT_OK;
+        return pfth::set_error(e, e == PFT_ERR_TIMEOUT ? "a wait of this batch sweep timed out"
+                                                       : "this batch sweep's kernel ran without its cluster shape");
+      }
+    }
     for (int i = 0; i < b->count; ++i) {
       pie_ctx* c = b->ctx[i];
       phi[i] = b->h_red[i] / ((double)c->npos * (double)c->n * (double)c->n);
@@ -1439,8 +1592,28 @@ int pie_batch_classes(const pie_batch* b, int* nclasses, int* launches_per_sweep
   *nclasses = (int)b->classes.size();
   if (launches_per_sweep) {
     int l = 0;
-    for (auto& cl : b->classes) l += (int)cl.col_off.size() - 1;
+    for (auto& cl : b->classes)
+      l += (b->mode == PIE_MODE_COLOURED && b->launch == PIE_LAUNCH_DATAFLOW && b->ctx[cl.rep]->kern_claim[0].fn)
+               ? 1 : (int)cl.col_off.size() - 1;
     *launches_per_sweep = l;
+  }
+  return PFT_OK;
+}
+
+int pie_batch_set_launch(pie_batch* b, int form) {
+  if (!b) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (form != PIE_LAUNCH_PER_COLOUR && form != PIE_LAUNCH_DATAFLOW)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "a batch launches per colour or as dataflow, not form %d", form);
+  if (b->mode != PIE_MODE_COLOURED)
+    return pfth::set_error(PFT_ERR_UNSUPPORTED, "launch forms apply to coloured batches");
+  if (b->launch != form) {
+    PFT_CUDA_TRY(cudaDeviceSynchronize());
+    b->launch = form;
+    for (auto& g : b->graphs) {
+      cudaGraphExecDestroy(g.exec);
+      cudaFree(g.d_inst);
+    }
+    b->graphs.clear();
   }
   return PFT_OK;
 }

@@ -11,18 +11,19 @@ constexpr int kThreads = 256;
 
 struct Entry {
   int N, mode, C;
+  bool claim;
   PieKernel k;
 };
 
-template <int N, int MODE, int C>
+template <int N, int MODE, int C, bool CLAIM = false>
 void add(std::vector<Entry>& v) {
   if constexpr (PieFullShape<N, C>::VALID) {
     PieKernel k;
-    k.fn = (const void*)k_pie_full<N, MODE, C, kThreads>;
+    k.fn = (const void*)k_pie_full<N, MODE, C, kThreads, CLAIM>;
     k.smem = PieFullShape<N, C>::SMEM;
     k.cluster = C;
     k.threads = kThreads;
-    v.push_back(Entry{N, MODE, C, k});
+    v.push_back(Entry{N, MODE, C, CLAIM, k});
   }
 }
 
@@ -32,6 +33,8 @@ void add_size(std::vector<Entry>& v) {
   add<N, MODE_COLOURED, 2>(v);
   add<N, MODE_COLOURED, 4>(v);
   add<N, MODE_COLOURED, 8>(v);
+  add<N, MODE_COLOURED, 4, true>(v);
+  add<N, MODE_COLOURED, 8, true>(v);
   add<N, MODE_BATCHED, 1>(v);
   add<N, MODE_BATCHED, 2>(v);
   add<N, MODE_BATCHED, 4>(v);
@@ -49,10 +52,10 @@ std::vector<Entry> build_table() {
 }  // namespace
 
 namespace pfth {
-PieKernel pie_full_kernel(int N, int mode, int C) {
+PieKernel pie_full_kernel(int N, int mode, int C, bool claim) {
   static const std::vector<Entry> table = build_table();
   for (const Entry& e : table)
-    if (e.N == N && e.mode == mode && e.C == C) return e.k;
+    if (e.N == N && e.mode == mode && e.C == C && e.claim == claim) return e.k;
   return PieKernel{};
 }
 }  // namespace pfth

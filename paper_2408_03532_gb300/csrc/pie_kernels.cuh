@@ -79,6 +79,12 @@ struct PieArgs {
   const int* dep_off;
   const int* dep;
   unsigned* done;           // [schedule length], zero at launch
+  // dataflow sweep with claimed items (ticket != nullptr): clusters take items
+  // in schedule order from *ticket (zero at launch) instead of item s going to
+  // cluster s mod (clusters). An item then only waits for items already claimed
+  // by running clusters, so every wait ends without the clusters being
+  // co-resident (used when several sweeps share the GPU).
+  unsigned* ticket;
 };
 
 template <int C>
@@ -381,7 +387,10 @@ struct PiePftShape {
   static constexpr size_t SMEM = sizeof(float2) * (OFF_D + (M * CM + 1) / 2);
 };
 
-template <int P, int Q, int MP, int MODE, int C, int NT>
+// CLAIM: the variant whose clusters claim items from PieArgs::ticket (dataflow
+// sweeps of several shape classes sharing the GPU); the others assign items
+// statically, without the claim's registers.
+template <int P, int Q, int MP, int MODE, int C, int NT, bool CLAIM = false>
 __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_pft(PieArgs a, const __grid_constant__ PftConst c,
                                                 const float2* __restrict__ gW, const float2* __restrict__ gtw) {
   using S = PiePftShape<P, Q, MP, C>;
@@ -426,12 +435,19 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
   const int step = gridDim.x / C;
   const bool persistent = MODE == MODE_COLOURED && a.ncol > 0;  // every colour in this launch
   const bool flow = persistent && a.dep_off != nullptr;         // per-item waits instead
+  const bool dyn = CLAIM && flow && a.ticket != nullptr;        // items claimed in schedule order
+  __shared__ int s_claim;
   const int ncol = persistent ? a.ncol : 1;
   int ce = persistent ? a.col_off[1] : a.count;
   int it = (persistent ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
   for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) cp_async8(sm + i, gW + i);
   fill_stage_table_async<P>(stw, gtw, P);
   cp_async_commit();
+  if (dyn) {
+    if (rank == 0 && threadIdx.x == 0) s_claim = (int)atomicAdd(a.ticket, 1u);
+    CL::sync();
+    it = *CL::map(&s_claim, 0u);
+  }
   if (it < ce) {
     const PieItem q = resolve<M * M>(a, it);
     gather_static(q);
@@ -450,7 +466,10 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
     if (!grid_barrier(a.gbar, (unsigned)col * gridDim.x, a.gerr, a.gstatus)) break;
     if (it < ce) gather_obj(resolve<M * M>(a, it));
   }
-  for (; it < ce; it += step) {
+  while (it < ce) {
+    int claimed = 0;  // the next item when items are claimed
+    unsigned tk = 0;
+    if (dyn && rank == 0 && threadIdx.x == 0) tk = atomicAdd(a.ticket, 1u);  // the next item, claimed early
     const PieItem p = resolve<M * M>(a, it);
     const long long obase = p.obase;
     for (int round = 0; round < rounds; ++round) {
@@ -475,7 +494,9 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
         dst[(t % CM) * S::SYT + u + u / Q] = val;
       });
     }
+    if (dyn && round == 0 && rank == 0 && threadIdx.x == 0) s_claim = (int)tk;
     CL::sync();
+    if (dyn && round == 0) claimed = *CL::map(&s_claim, 0u);
     // 3a. columns (axis 1) of this CTA's slice
     for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
       const int tl = cs0 + g;
@@ -529,13 +550,15 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
     if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
     }  // round
     if (flow) signal_done(a, it);
-    if (it + step < ce) {  // the next item of this colour
-      const PieItem q = resolve<M * M>(a, it + step);
+    const int nxt = dyn ? claimed : it + step;
+    if (nxt < ce) {  // the next item of this colour
+      const PieItem q = resolve<M * M>(a, nxt);
       gather_static(q);
-      if (flow) wait_deps<C>(a, it + step);
+      if (flow) wait_deps<C>(a, nxt);
       gather_obj(q);
     }
     if constexpr (C == 1) __syncthreads();
+    it = nxt;
   }
   if (col + 1 < ncol) {  // the next colour's first item: all but the object before the barrier
     ce = a.col_off[col + 2];
@@ -578,7 +601,7 @@ struct PieFullShape {
   static constexpr size_t SMEM = sizeof(float2) * (OFF_D + (N * CN + 1) / 2);
 };
 
-template <int N, int MODE, int C, int NT>
+template <int N, int MODE, int C, int NT, bool CLAIM = false>
 __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(PieArgs a, const float2* __restrict__ gtw) {
   using S = PieFullShape<N, C, NT>;
   using F = typename S::F;
@@ -619,11 +642,18 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
   const int step = gridDim.x / C;
   const bool persistent = MODE == MODE_COLOURED && a.ncol > 0;  // every colour in this launch
   const bool flow = persistent && a.dep_off != nullptr;         // per-item waits instead
+  const bool dyn = CLAIM && flow && a.ticket != nullptr;        // items claimed in schedule order
+  __shared__ int s_claim;
   const int ncol = persistent ? a.ncol : 1;
   int ce = persistent ? a.col_off[1] : a.count;
   int it = (persistent ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
   F::fill_async(tw, gtw);
   cp_async_commit();
+  if (dyn) {
+    if (rank == 0 && threadIdx.x == 0) s_claim = (int)atomicAdd(a.ticket, 1u);
+    CL::sync();
+    it = *CL::map(&s_claim, 0u);
+  }
   if (it < ce) {
     const PieItem q = resolve<N * N>(a, it);
     gather_static(q);
@@ -642,7 +672,10 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
     if (!grid_barrier(a.gbar, (unsigned)col * gridDim.x, a.gerr, a.gstatus)) break;
     if (it < ce) gather_obj(resolve<N * N>(a, it));
   }
-  for (; it < ce; it += step) {
+  while (it < ce) {
+    int claimed = 0;  // the next item when items are claimed
+    unsigned tk = 0;
+    if (dyn && rank == 0 && threadIdx.x == 0) tk = atomicAdd(a.ticket, 1u);  // the next item, claimed early
     const PieItem p = resolve<N * N>(a, it);
     const long long obase = p.obase;
     for (int round = 0; round < rounds; ++round) {
@@ -669,7 +702,9 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
         CL::map(sC, (unsigned)(s / CN))[u * S::SCS + s % CN] = x[p];
       }
     }
+    if (dyn && round == 0 && rank == 0 && threadIdx.x == 0) s_claim = (int)tk;
     CL::sync();
+    if (dyn && round == 0) claimed = *CL::map(&s_claim, 0u);
     // 3a. FFT of the local slot columns (rows in natural order -> slot order)
     for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
       const int b = b0 + g;
@@ -729,13 +764,15 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
     if (rounds == 2 && round == 0) __syncthreads();  // updated patch visible to the second round
     }  // round
     if (flow) signal_done(a, it);
-    if (it + step < ce) {  // the next item of this colour
-      const PieItem q = resolve<N * N>(a, it + step);
+    const int nxt = dyn ? claimed : it + step;
+    if (nxt < ce) {  // the next item of this colour
+      const PieItem q = resolve<N * N>(a, nxt);
       gather_static(q);
-      if (flow) wait_deps<C>(a, it + step);
+      if (flow) wait_deps<C>(a, nxt);
       gather_obj(q);
     }
     if constexpr (C == 1) __syncthreads();
+    it = nxt;
   }
   if (col + 1 < ncol) {  // the next colour's first item: all but the object before the barrier
     ce = a.col_off[col + 2];
@@ -759,7 +796,9 @@ struct PieKernel {
 }  // namespace pftk
 
 namespace pfth {
-// PIE kernels for a (transform, shape, mode, cluster size); fn == nullptr if not built.
-pftk::PieKernel pie_pft_kernel(int P, int Q, int MP, int mode, int C);
-pftk::PieKernel pie_full_kernel(int N, int mode, int C);
+// PIE kernels for a (transform, shape, mode, cluster size); fn == nullptr if not
+// built. claim: the coloured-mode variant that claims items (built for 4 and 8
+// CTAs per position).
+pftk::PieKernel pie_pft_kernel(int P, int Q, int MP, int mode, int C, bool claim = false);
+pftk::PieKernel pie_full_kernel(int N, int mode, int C, bool claim = false);
 }  // namespace pfth

@@ -11,18 +11,19 @@ constexpr int kThreads = 256;
 
 struct Entry {
   int P, Q, MP, mode, C;
+  bool claim;
   PieKernel k;
 };
 
-template <int P, int Q, int MP, int MODE, int C>
+template <int P, int Q, int MP, int MODE, int C, bool CLAIM = false>
 void add(std::vector<Entry>& v) {
   if constexpr (PiePftShape<P, Q, MP, C>::VALID) {
     PieKernel k;
-    k.fn = (const void*)k_pie_pft<P, Q, MP, MODE, C, kThreads>;
+    k.fn = (const void*)k_pie_pft<P, Q, MP, MODE, C, kThreads, CLAIM>;
     k.smem = PiePftShape<P, Q, MP, C>::SMEM;
     k.cluster = C;
     k.threads = kThreads;
-    v.push_back(Entry{P, Q, MP, MODE, C, k});
+    v.push_back(Entry{P, Q, MP, MODE, C, CLAIM, k});
   }
 }
 
@@ -32,6 +33,8 @@ void add_shape(std::vector<Entry>& v) {
   add<P, Q, MP, MODE_COLOURED, 2>(v);
   add<P, Q, MP, MODE_COLOURED, 4>(v);
   add<P, Q, MP, MODE_COLOURED, 8>(v);
+  add<P, Q, MP, MODE_COLOURED, 4, true>(v);
+  add<P, Q, MP, MODE_COLOURED, 8, true>(v);
   add<P, Q, MP, MODE_BATCHED, 1>(v);
   add<P, Q, MP, MODE_BATCHED, 2>(v);
   add<P, Q, MP, MODE_BATCHED, 4>(v);
@@ -56,10 +59,10 @@ std::vector<Entry> build_table() {
 }  // namespace
 
 namespace pfth {
-PieKernel pie_pft_kernel(int P, int Q, int MP, int mode, int C) {
+PieKernel pie_pft_kernel(int P, int Q, int MP, int mode, int C, bool claim) {
   static const std::vector<Entry> table = build_table();
   for (const Entry& e : table)
-    if (e.P == P && e.Q == Q && e.MP == MP && e.mode == mode && e.C == C) return e.k;
+    if (e.P == P && e.Q == Q && e.MP == MP && e.mode == mode && e.C == C && e.claim == claim) return e.k;
   return PieKernel{};
 }
 }  // namespace pfth

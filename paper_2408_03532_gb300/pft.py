@@ -122,6 +122,7 @@ def load() -> ctypes.CDLL:
         "pie_batch_destroy": (ctypes.c_int, [_P]),
         "pie_batch_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
         "pie_batch_classes": (ctypes.c_int, [_P, _P, _P]),
+        "pie_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -460,6 +461,11 @@ class PieBatch:
         nc, nl = ctypes.c_int(), ctypes.c_int()
         _check(load().pie_batch_classes(self._h, ctypes.byref(nc), ctypes.byref(nl)))
         return nc.value, nl.value
+
+    def set_launch(self, form: int):
+        """Coloured batches: LAUNCH_PER_COLOUR (one launch per class and
+        colour, the default) or LAUNCH_DATAFLOW (one launch per class and sweep)."""
+        _check(load().pie_batch_set_launch(self._h, int(form)))
 
     def iteration(self, objects, transform: int = TRANSFORM_PFT, beta: float = 1.0, stats: bool = True,
                   stream=None):

@@ -1,5 +1,5 @@
 """Independent reconstructions of different sizes swept together (one CUDA
-graph per sweep, one launch per shape class and colour)."""
+graph per sweep; one launch per shape class, or per class and colour)."""
 import numpy as np
 import pytest
 
@@ -75,11 +75,36 @@ def test_small_batch_matches_oracle_per_instance(env, mode, transform):
         assert phi[i] == pytest.approx(po, rel=TOL)
 
 
+def test_dataflow_batch_equals_per_colour_launches(env):
+    """The coloured batch in its two launch forms (one dataflow launch per
+    class, or one launch per class and colour) gives the same objects bit for
+    bit over two sweeps; the dataflow form makes one launch per class."""
+    torch, pft = env
+    insts = small_instances()
+    A = pft.PieBatch(to_gpu(insts, torch))
+    B = pft.PieBatch(to_gpu(insts, torch))
+    A.set_launch(pft.LAUNCH_PER_COLOUR)
+    B.set_launch(pft.LAUNCH_DATAFLOW)
+    assert B.classes() == (4, 4)
+    assert A.classes()[1] > 4
+    za = [torch.from_numpy(i["init"].astype(np.complex64)).cuda() for i in insts]
+    zb = [z.clone() for z in za]
+    for _ in range(2):
+        pa = A.iteration(za, pft.TRANSFORM_PFT, 0.9)
+        pb = B.iteration(zb, pft.TRANSFORM_PFT, 0.9)
+    for i in range(len(insts)):
+        assert torch.equal(za[i], zb[i]), i
+        assert pb[i] == pytest.approx(pa[i], rel=1e-6)
+    with pytest.raises(pft.PftError):
+        B.set_launch(pft.LAUNCH_PERSISTENT)
+
+
 def test_batch_equals_separate_contexts_at_full_recipe(env):
     """The 64-instance recipe (objects 256^2-2048^2, probes 64^2-256^2, 50-2000
     Fermat positions, M in {16, 32, 64}): one batched PFT sweep gives, instance
     by instance, exactly the object of a sweep with a context of its own (the
-    same kernel on the same data; only the launch grouping differs)."""
+    same kernel on the same data; only the launch grouping differs), in both
+    coloured launch forms."""
     torch, pft = env
     specs = synth.uneven_batch_recipe(64)
     insts = []
@@ -92,10 +117,16 @@ def test_batch_equals_separate_contexts_at_full_recipe(env):
                           intensities=inten, M=sp["M"], init=inst["init"]))
     B = pft.PieBatch(insts)
     nclass, nlaunch = B.classes()
-    assert nclass >= 5
+    assert nclass >= 5 and nlaunch > nclass  # one launch per class and colour
     objs = [torch.from_numpy(i["init"].astype(np.complex64)).cuda() for i in insts]
     B.iteration(objs, pft.TRANSFORM_PFT, 1.0, stats=False)
+    B.set_launch(pft.LAUNCH_DATAFLOW)  # and one dataflow launch per class
+    assert B.classes() == (nclass, nclass)
+    objs_flow = [torch.from_numpy(i["init"].astype(np.complex64)).cuda() for i in insts]
+    B.iteration(objs_flow, pft.TRANSFORM_PFT, 1.0, stats=False)
     torch.cuda.synchronize()
+    for i in range(len(insts)):
+        assert torch.equal(objs_flow[i], objs[i]), i
     for i in (0, 17, 41, 63):
         ctx = pft.PieContext(insts[i]["obj_shape"], insts[i]["probe"], insts[i]["positions"],
                              insts[i]["intensities"], M=insts[i]["M"], autotune=False)
