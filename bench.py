@@ -384,7 +384,9 @@ def main() -> None:
     peak = alu_peak_tflops()
     achieved = dom[2] / (dom[1] / 1e3) / 1e12
     roof = {"bound": "alu", "kernel": dom[0], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": _pie_traffic(dom[0], len(P["pos"])),
+            "traffic_note": "DRAM bytes per sweep, scaled by positions from an ncu capture (--cache-control none) "
+                            "of single-colour launches; the object and probe stay in L2",
             "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, no measured SIMT peak)",
             "launches_per_sweep": {"pie_pft": kernel_launches(mode, ncol, tuning, "pft"),
                                    "pie_full": kernel_launches(mode, ncol, tuning, "full")},
@@ -498,6 +500,35 @@ def _csrc_sha(name: str) -> str:
     import hashlib
     path = os.path.join(ROOT, "paper_2408_03532_gb300", "csrc", name)
     return hashlib.sha256(open(path, "rb").read()).hexdigest()
+
+
+# DRAM traffic (read + write bytes per scan position) of the fused PIE kernels on
+# the 1024^2 / 128^2 / 3600-position workload: ncu with --cache-control none on
+# four launches of one colour each (31-33 positions; one-launch-per-colour
+# form, the same kernel code as the single-launch sweeps), averaged over their
+# 128 positions. Reads are the amplitudes (4 M^2 = 4096 B, 4 n^2 = 65536 B):
+# the object and probe stay in L2. The PFT kernel's writes are L2 evictions of
+# dirty lines (earlier object updates and the L2 flush buffer). Valid only for
+# the sources they were taken on.
+PIE_TRAFFIC = {
+    "pie_pft": {"sources": {"pie_kernels.cuh": "43734f7cebade0149480b31d539ce8d594c3e267e8ffc2cd2b2afd6eed57d819",
+                            "pft_core.cuh": "8e1db7fdcbf044cf493f01e80163628327931b8efe774c64fd96074c7f8ea072",
+                            "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
+                "read_per_position": 529920 / 128, "write_per_position": 1408768 / 128},
+    "pie_full": {"sources": {"pie_kernels.cuh": "43734f7cebade0149480b31d539ce8d594c3e267e8ffc2cd2b2afd6eed57d819",
+                             "fft_core.cuh": "09cb4b087056aa59c79069c8ed564712ebff83ebb98a195e5682d47eb335d05e",
+                             "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
+                 "read_per_position": 8501248 / 128, "write_per_position": 56576 / 128},
+}
+
+
+def _pie_traffic(kernel: str, positions: int):
+    """DRAM bytes of one sweep's launch of `kernel` (scaled from the per-position
+    capture), or None when a source changed since the capture."""
+    rec = PIE_TRAFFIC.get(kernel)
+    if rec is None or any(_csrc_sha(f) != h for f, h in rec["sources"].items()):
+        return None
+    return (rec["read_per_position"] + rec["write_per_position"]) * positions
 
 
 def _traffic(kernel: str, frames: int):
