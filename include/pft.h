@@ -239,6 +239,31 @@ int pie_ctx_info_get(const pie_ctx* ctx, pie_ctx_info* info);
  * colour of each position (host int32 [N], may be NULL). */
 int pie_ctx_colours(const pie_ctx* ctx, int* ncolours, int32_t* colour_of);
 
+/* Host only (no GPU work, no allocation on the device): the order in which a
+ * context with these positions sweeps them. The paper visits positions
+ * sequentially (Section 2.1, Eq. pie_update); any visiting order is a valid
+ * PIE order, and the library runs the positions colour by colour:
+ *   colour   host int32 [npos]: greedy colouring in visiting order (each
+ *            position takes the smallest colour unused by an earlier visited
+ *            position whose patch overlaps its own; patches overlap when both
+ *            corner coordinates differ by less than n);
+ *   sched    host int32 [npos]: the colour-major schedule, visiting order
+ *            within a colour (what every coloured sweep runs);
+ *   dep_off  host int32 [npos + 1], dep host int32 [dep_capacity]: the
+ *            predecessors of schedule item s (schedule indices
+ *            dep[dep_off[s] .. dep_off[s + 1])) that the dataflow launch form
+ *            waits for: the earlier items whose patches overlap item s, minus
+ *            those that are also earlier overlapping items of another member
+ *            of that set (waiting for the later one covers them).
+ * positions: host int32 [npos][2] top-left (row, col), each patch inside the
+ * obj_h x obj_w object; order: host int32 [npos] permutation or NULL (index
+ * order). *ncolours and *ndep (the number of dep entries) are always written;
+ * every other output may be NULL. INVALID_ARG for a patch outside the object,
+ * an order that is not a permutation, or dep_capacity < *ndep with dep set. */
+int pie_scan_schedule(const int32_t* positions, int npos, int n, int obj_h, int obj_w, const int32_t* order,
+                      int* ncolours, int32_t* colour, int32_t* sched, int32_t* dep_off, int32_t* dep,
+                      int64_t dep_capacity, int64_t* ndep);
+
 /* One PIE sweep over all positions (Eq. pie_update with Eq. 3), in place on
  * `object` (device [obj_h][obj_w] complex). transform: PIE_TRANSFORM_*.
  * Step: beta * conj(w) / max|w|^2 (coloured) or

@@ -319,86 +319,74 @@ int prepare_kernel(const PieKernel& k, long long* cap) {
   return PFT_OK;
 }
 
-// Greedy colouring in visiting order (smallest colour unused by an earlier
-// visited overlapping patch); colour-major schedule, visiting order within a
-// colour. `order` is a permutation of 0..N-1 (empty: index order).
-void colour_positions(pie_ctx* c, const std::vector<int>& order = {}) {
-  const int N = c->npos, n = c->n;
-  c->colour.assign(N, -1);
-  // bucket positions by n x n cells so only neighbouring cells are scanned
-  const int cw = (c->W + n - 1) / n + 1, ch = (c->H + n - 1) / n + 1;
+// The order of a coloured sweep, built on the host from the scan alone:
+//  - greedy colouring in visiting order (each position takes the smallest colour
+//    unused by an earlier visited position whose patch overlaps its own);
+//  - the colour-major schedule, visiting order within a colour;
+//  - the dataflow predecessors of schedule item s: E(s) = the earlier schedule
+//    items whose patches overlap item s (all of an earlier colour), minus every
+//    b of E(s) that is also in E(a) for some a of E(s) (a itself waited for b
+//    before it ran, so waiting for a covers b, by induction along the schedule).
+// Patches are n x n with top-left corners pos[j] = (row, col) inside H x W;
+// `order` is a permutation of 0..N-1 (empty: index order).
+struct PieSchedule {
+  std::vector<int> visit, colour, col_off, sched, dep_off, dep;
+  int ncol = 0;
+};
+
+void build_schedule(const std::vector<int2>& pos, int n, int H, int W, const std::vector<int>& order,
+                    PieSchedule& out) {
+  const int N = (int)pos.size();
+  // positions bucketed by n x n cells: overlapping patches lie in neighbouring cells
+  const int cw = (W + n - 1) / n + 1, ch = (H + n - 1) / n + 1;
+  auto overlap = [&](int2 p, int2 q) { return std::abs(q.x - p.x) < n && std::abs(q.y - p.y) < n; };
+  auto for_neighbours = [&](const std::vector<std::vector<int>>& cells, int2 p, auto&& f) {
+    const int cx = p.y / n, cy = p.x / n;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int yy = cy + dy, xx = cx + dx;
+        if (yy < 0 || xx < 0 || yy >= ch || xx >= cw) continue;
+        for (int i : cells[(size_t)yy * cw + xx]) f(i);
+      }
+  };
+  out.colour.assign(N, -1);
+  out.visit.resize(N);
+  for (int a = 0; a < N; ++a) out.visit[a] = order.empty() ? a : order[a];
   std::vector<std::vector<int>> cells((size_t)cw * ch);
   std::vector<char> used;
   int ncol = 0;
-  c->visit.resize(N);
-  for (int a = 0; a < N; ++a) c->visit[a] = order.empty() ? a : order[a];
   for (int a = 0; a < N; ++a) {
-    const int j = c->visit[a];
-    const int2 p = c->h_pos[j];
-    const int cx = p.y / n, cy = p.x / n;
+    const int j = out.visit[a];
+    const int2 p = pos[j];
     used.assign(ncol + 1, 0);
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int yy = cy + dy, xx = cx + dx;
-        if (yy < 0 || xx < 0 || yy >= ch || xx >= cw) continue;
-        for (int i : cells[(size_t)yy * cw + xx]) {
-          const int2 q = c->h_pos[i];
-          if (std::abs(q.x - p.x) < n && std::abs(q.y - p.y) < n) used[c->colour[i]] = 1;
-        }
-      }
+    for_neighbours(cells, p, [&](int i) {
+      if (overlap(p, pos[i])) used[out.colour[i]] = 1;
+    });
     int col = 0;
     while (col < ncol && used[col]) ++col;
-    c->colour[j] = col;
+    out.colour[j] = col;
     if (col == ncol) ++ncol;
-    cells[(size_t)cy * cw + cx].push_back(j);
+    cells[(size_t)(p.x / n) * cw + p.y / n].push_back(j);
   }
-  c->ncol = ncol;
-  c->col_off.assign(ncol + 1, 0);
-  for (int j = 0; j < N; ++j) c->col_off[c->colour[j] + 1]++;
-  for (int k = 0; k < ncol; ++k) c->col_off[k + 1] += c->col_off[k];
-}
-
-// Launches the fused kernel for `a.count` positions. Coloured sweeps pick the
-// largest cluster size whose CTAs for all positions of the colour fit on the
-// GPU at once; the other modes run one CTA per position.
-// Colour-major schedule (visiting order inside a colour) to the device.
-int upload_schedule(pie_ctx* c, cudaStream_t st) {
-  std::vector<int> sched(c->npos);
-  std::vector<int> fill(c->col_off.begin(), c->col_off.end() - 1);
-  for (int j : c->visit) sched[fill[c->colour[j]]++] = j;
-  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_sched, sched.data(), sizeof(int) * c->npos, cudaMemcpyHostToDevice, st));
-  cudaFree(c->d_coloff);
-  c->d_coloff = nullptr;
-  PFT_CUDA_TRY(cudaMalloc(&c->d_coloff, sizeof(int) * c->col_off.size()));
-  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_coloff, c->col_off.data(), sizeof(int) * c->col_off.size(),
-                               cudaMemcpyHostToDevice, st));
-  c->max_colour = 0;
-  for (int k = 0; k < c->ncol; ++k) c->max_colour = std::max(c->max_colour, c->col_off[k + 1] - c->col_off[k]);
-  // dataflow predecessors: E(s) = the earlier schedule items whose patches
-  // overlap item s (all of an earlier colour). An item b of E(s) that is also in
-  // E(a) for some a of E(s) is dropped: a itself waited for b before it ran, so
-  // waiting for a covers b (by induction along the schedule).
-  const int N = c->npos, n = c->n;
-  std::vector<int> inv(N);
-  for (int s = 0; s < N; ++s) inv[sched[s]] = s;
-  const int cw = (c->W + n - 1) / n + 1, ch = (c->H + n - 1) / n + 1;
-  std::vector<std::vector<int>> cells((size_t)cw * ch);
+  out.ncol = ncol;
+  out.col_off.assign(ncol + 1, 0);
+  for (int j = 0; j < N; ++j) out.col_off[out.colour[j] + 1]++;
+  for (int k = 0; k < ncol; ++k) out.col_off[k + 1] += out.col_off[k];
+  out.sched.assign(N, 0);
+  std::vector<int> fill(out.col_off.begin(), out.col_off.end() - 1);
+  for (int j : out.visit) out.sched[fill[out.colour[j]]++] = j;
+  // predecessors in schedule indices
+  for (auto& cell : cells) cell.clear();
   std::vector<std::vector<int>> E(N);
   for (int s = 0; s < N; ++s) {
-    const int2 p = c->h_pos[sched[s]];
-    const int cx = p.y / n, cy = p.x / n;
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int yy = cy + dy, xx = cx + dx;
-        if (yy < 0 || xx < 0 || yy >= ch || xx >= cw) continue;
-        for (int i : cells[(size_t)yy * cw + xx]) {
-          const int2 q = c->h_pos[sched[i]];
-          if (std::abs(q.x - p.x) < n && std::abs(q.y - p.y) < n) E[s].push_back(i);
-        }
-      }
-    cells[(size_t)cy * cw + cx].push_back(s);
+    const int2 p = pos[out.sched[s]];
+    for_neighbours(cells, p, [&](int i) {
+      if (overlap(p, pos[out.sched[i]])) E[s].push_back(i);
+    });
+    cells[(size_t)(p.x / n) * cw + p.y / n].push_back(s);
   }
-  std::vector<int> off(N + 1, 0), dep;
+  out.dep_off.assign(N + 1, 0);
+  out.dep.clear();
   std::vector<char> mark(N, 0);  // 1: in E(s), 2: covered by another member of E(s)
   for (int s = 0; s < N; ++s) {
     for (int b : E[s]) mark[b] = 1;
@@ -406,14 +394,40 @@ int upload_schedule(pie_ctx* c, cudaStream_t st) {
       for (int b : E[a])
         if (mark[b]) mark[b] = 2;
     for (int b : E[s]) {
-      if (mark[b] == 1) dep.push_back(b);
+      if (mark[b] == 1) out.dep.push_back(b);
       mark[b] = 0;
     }
-    off[s + 1] = (int)dep.size();
+    out.dep_off[s + 1] = (int)out.dep.size();
   }
-  c->h_dep_off = off;
-  c->h_dep = dep;
-  c->h_sched = sched;
+}
+
+// The context's colouring and schedule for a visiting order (empty: index order).
+void colour_positions(pie_ctx* c, const std::vector<int>& order = {}) {
+  PieSchedule sch;
+  build_schedule(c->h_pos, c->n, c->H, c->W, order, sch);
+  c->visit = std::move(sch.visit);
+  c->colour = std::move(sch.colour);
+  c->col_off = std::move(sch.col_off);
+  c->ncol = sch.ncol;
+  c->h_sched = std::move(sch.sched);
+  c->h_dep_off = std::move(sch.dep_off);
+  c->h_dep = std::move(sch.dep);
+}
+
+// The colour-major schedule, colour offsets and dataflow predecessor lists to
+// the device.
+int upload_schedule(pie_ctx* c, cudaStream_t st) {
+  const int N = c->npos;
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_sched, c->h_sched.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  cudaFree(c->d_coloff);
+  c->d_coloff = nullptr;
+  PFT_CUDA_TRY(cudaMalloc(&c->d_coloff, sizeof(int) * c->col_off.size()));
+  PFT_CUDA_TRY(cudaMemcpyAsync(c->d_coloff, c->col_off.data(), sizeof(int) * c->col_off.size(),
+                               cudaMemcpyHostToDevice, st));
+  c->max_colour = 0;
+  for (int k = 0; k < c->ncol; ++k) c->max_colour = std::max(c->max_colour, c->col_off[k + 1] - c->col_off[k]);
+  const std::vector<int>& off = c->h_dep_off;
+  const std::vector<int>& dep = c->h_dep;
   cudaFree(c->d_dep_off);
   cudaFree(c->d_dep);
   cudaFree(c->d_done);
@@ -433,6 +447,9 @@ int upload_schedule(pie_ctx* c, cudaStream_t st) {
   return PFT_OK;
 }
 
+// Launches the fused kernel for `a.count` positions. Coloured sweeps pick the
+// largest cluster size whose CTAs for all positions of the colour fit on the
+// GPU at once; the other modes run one CTA per position.
 int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) {
   if (a.count <= 0) return PFT_OK;
   const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
@@ -830,6 +847,46 @@ int pie_ctx_info_get(const pie_ctx* c, pie_ctx_info* info) {
     if (c->persist[t] != PIE_LAUNCH_DATAFLOW || c->flow_ci[t] < 0) continue;
     (t == 0 ? info->cluster_pft : info->cluster_full) = 1 << c->flow_ci[t];
   }
+  return PFT_OK;
+}
+
+int pie_scan_schedule(const int32_t* positions, int npos, int n, int obj_h, int obj_w, const int32_t* order,
+                      int* ncolours, int32_t* colour, int32_t* sched, int32_t* dep_off, int32_t* dep,
+                      int64_t dep_capacity, int64_t* ndep) {
+  if (!positions || !ncolours || !ndep) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (npos < 1 || n < 1 || obj_h < n || obj_w < n)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "need npos >= 1 and an n x n patch inside the object");
+  std::vector<int2> pos(npos);
+  for (int j = 0; j < npos; ++j) {
+    const int r = positions[2 * j], q = positions[2 * j + 1];
+    if (r < 0 || q < 0 || r + n > obj_h || q + n > obj_w)
+      return pfth::set_error(PFT_ERR_INVALID_ARG, "position %d (%d, %d) puts the patch outside the object", j, r, q);
+    pos[j] = make_int2(r, q);
+  }
+  std::vector<int> ord;
+  if (order) {
+    ord.assign(order, order + npos);
+    std::vector<char> seen(npos, 0);
+    for (int j : ord) {
+      if (j < 0 || j >= npos || seen[j]) return pfth::set_error(PFT_ERR_INVALID_ARG, "order is not a permutation");
+      seen[j] = 1;
+    }
+  }
+  PieSchedule sch;
+  build_schedule(pos, n, obj_h, obj_w, ord, sch);
+  *ncolours = sch.ncol;
+  *ndep = (int64_t)sch.dep.size();
+  if (dep && dep_capacity < (int64_t)sch.dep.size())
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "dep holds %lld entries, %lld needed", (long long)dep_capacity,
+                           (long long)sch.dep.size());
+  for (int j = 0; j < npos; ++j) {
+    if (colour) colour[j] = sch.colour[j];
+    if (sched) sched[j] = sch.sched[j];
+  }
+  if (dep_off)
+    for (int s = 0; s <= npos; ++s) dep_off[s] = sch.dep_off[s];
+  if (dep)
+    for (size_t i = 0; i < sch.dep.size(); ++i) dep[i] = sch.dep[i];
   return PFT_OK;
 }
 

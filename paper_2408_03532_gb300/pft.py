@@ -123,6 +123,8 @@ def load() -> ctypes.CDLL:
         "pie_batch_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
         "pie_batch_classes": (ctypes.c_int, [_P, _P, _P]),
         "pie_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int]),
+        "pie_scan_schedule": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                             _P, _P, ctypes.c_int64, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -274,6 +276,29 @@ def nrmse_noalloc(obj, truth, mask=None, stream=None) -> float:
 
 
 # --------------------------------------------------------------------- PIE
+def pie_scan_schedule(positions, n: int, obj_shape, order=None) -> dict:
+    """The order a coloured sweep visits the positions in (host only, no GPU):
+    greedy colours, the colour-major schedule and each schedule item's dataflow
+    predecessors (schedule indices). Returns a dict with ncolours, colour,
+    sched, dep_off and dep (numpy int32 arrays)."""
+    lib = load()
+    pos = np.ascontiguousarray(np.asarray(positions, dtype=np.int32).reshape(-1, 2))
+    N = len(pos)
+    o = None if order is None else np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    if o is not None and o.shape != (N,):
+        raise ValueError("order must be a permutation of the positions")
+    h, w = obj_shape
+    ncol, ndep = ctypes.c_int(), ctypes.c_int64()
+    _check(lib.pie_scan_schedule(pos.ctypes.data, N, int(n), int(h), int(w), None if o is None else o.ctypes.data,
+                                 ctypes.byref(ncol), None, None, None, None, 0, ctypes.byref(ndep)))
+    colour, sched = np.empty(N, np.int32), np.empty(N, np.int32)
+    dep_off, dep = np.empty(N + 1, np.int32), np.empty(max(1, ndep.value), np.int32)
+    _check(lib.pie_scan_schedule(pos.ctypes.data, N, int(n), int(h), int(w), None if o is None else o.ctypes.data,
+                                 ctypes.byref(ncol), colour.ctypes.data, sched.ctypes.data, dep_off.ctypes.data,
+                                 dep.ctypes.data, len(dep), ctypes.byref(ndep)))
+    return {"ncolours": ncol.value, "colour": colour, "sched": sched, "dep_off": dep_off, "dep": dep[:ndep.value]}
+
+
 @dataclass
 class Schedule:
     beta_pft: float = 1.0
