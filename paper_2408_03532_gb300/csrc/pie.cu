@@ -494,9 +494,6 @@ int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) 
   return PFT_OK;
 }
 
-// One coloured sweep as a single cooperative launch: as many clusters as fit
-// on the GPU at once (at most the largest colour), looping over the colours
-// with a grid barrier in between (same kernel as the per-colour launches).
 // Cluster size (log2) of a persistent coloured sweep: the autotuned one, else
 // the largest built (-1: none).
 int persist_ci(const pie_ctx* c, int t) {
@@ -506,7 +503,10 @@ int persist_ci(const pie_ctx* c, int t) {
   return -1;
 }
 
-// The dataflow form (PIE_LAUNCH_DATAFLOW) runs the same kernel over the whole
+// One coloured sweep as a single cooperative launch of the per-colour kernel.
+// The persistent form (PIE_LAUNCH_PERSISTENT): as many clusters as fit on the
+// GPU at once (at most the largest colour) loop over the colours with a grid
+// barrier in between. The dataflow form (PIE_LAUNCH_DATAFLOW) runs the whole
 // colour-major schedule as one list, item s going to cluster s mod (clusters):
 // every item waits only for its overlapping predecessors instead of a barrier
 // per colour, so items of consecutive colours overlap in time. The result is

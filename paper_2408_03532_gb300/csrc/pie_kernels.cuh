@@ -14,8 +14,11 @@
 //   4. cluster barrier;
 //   5. rows: the adjoint row transform gives A^H R on CTA c's rows, and the
 //      object update z -= beta conj(w) / max|w|^2 . A^H R / n^2 is applied.
-// With C = 1 the cluster is one CTA and the two exchange buffers alias. The
-// barriers are the hardware cluster barrier; there is no spin wait.
+// With C = 1 the cluster is one CTA and the two exchange buffers alias. Within
+// a position the barriers are the hardware cluster barrier. Between positions,
+// a coloured sweep launched once per colour needs no wait; the single-launch
+// forms wait on a grid barrier per colour or on the completion counters of a
+// position's overlapping predecessors (both bounded spin waits, below).
 #pragma once
 
 #include <cooperative_groups.h>
