@@ -13,7 +13,8 @@ def _rand(shape, seed=0):
 
 def test_full_update_is_the_modulus_projection():
     """With w = 1 and beta = 1, one FULL update replaces the patch by P_M(z)
-    (Eq. 3), whose Fourier modulus is exactly d."""
+    (Eq. 3): its spectrum is d with the phase of the old patch's spectrum
+    (the modulus alone would also be d for -P_M(z))."""
     n = 16
     obj = _rand((24, 24), 1)
     probe = np.ones((n, n), complex)
@@ -21,6 +22,8 @@ def test_full_update_is_the_modulus_projection():
     z = obj.copy()
     pie.pie_update(z, probe, (3, 5), d, pie.full_transform(n, n), 1.0, 1.0)
     assert np.allclose(np.abs(np.fft.fft2(z[3:3 + n, 5:5 + n])), d, rtol=1e-12, atol=1e-12)
+    old = np.fft.fft2(obj[3:3 + n, 5:5 + n])
+    assert np.allclose(np.fft.fft2(z[3:3 + n, 5:5 + n]), d * old / np.abs(old), rtol=1e-12, atol=1e-12)
     # pixels outside the patch are untouched
     mask = np.ones_like(obj, bool)
     mask[3:3 + n, 5:5 + n] = False
@@ -103,6 +106,22 @@ def test_batched_equals_sequential_without_overlap():
     zb, fb = pie.batched_sweep(obj, probe, pos, d, T, 0.9, delta_rel=0.0)
     assert np.allclose(zs, zb, atol=1e-13)
     assert fs == pytest.approx(fb, rel=1e-12)
+
+
+def test_batched_step_projects_a_single_exit_wave():
+    """One position, delta = 0, beta = 1, FULL: the batched step divides by the
+    illumination |w|^2, so z <- z - conj(w) (w z - P_M(z)) / |w|^2 makes the new
+    exit wave w z exactly P_M(z) (Eq. 3) for any probe without zeros."""
+    n = 16
+    obj = _rand((n, n), 12)          # the patch covers the object (no unlit pixel to divide by 0)
+    rng = np.random.default_rng(13)
+    probe = (0.3 + rng.random((n, n))) * np.exp(2j * np.pi * rng.random((n, n)))
+    d = rng.random((1, n, n)) + 0.1
+    pos = np.array([[0, 0]], dtype=np.int32)
+    z, _ = pie.batched_sweep(obj, probe, pos, d, pie.full_transform(n, n), 1.0, delta_rel=0.0)
+    old = np.fft.fft2(probe * obj)
+    new = np.fft.fft2(probe * z)
+    assert np.allclose(new, d[0] * old / np.abs(old), rtol=1e-12, atol=1e-12)
 
 
 def test_noise_free_recovery_up_to_global_phase():
