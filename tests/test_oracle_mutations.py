@@ -258,3 +258,39 @@ def test_tv_with_a_backward_difference_adjoint(monkeypatch):
         return out
     monkeypatch.setattr(tv, "dx_adjoint", bad)
     fails(t_tv.test_difference_adjoints)
+
+
+def test_tv_step_uphill(monkeypatch):
+    monkeypatch.setattr(tv, "tv_step", lambda z, lam, eps: z + lam * tv.tv_grad(z, eps))
+    fails(t_tv.test_constant_and_ramp)
+
+
+# ---------------------------------------------------------------- metrics and the offline phase
+def test_error_metric_that_ignores_its_mask(monkeypatch):
+    orig = pie.nrmse
+    monkeypatch.setattr(pie, "nrmse", lambda z, truth, mask=None: orig(z, truth))
+    fails(t_pie.test_error_metrics_closed_forms)
+
+
+def test_relative_change_against_the_new_iterate(monkeypatch):
+    monkeypatch.setattr(pie, "relative_change",
+                        lambda new, old: float(np.linalg.norm(new - old) / np.linalg.norm(new)))
+    fails(t_pie.test_error_metrics_closed_forms)
+
+
+def test_one_term_too_many(monkeypatch):
+    orig = coeffs.choose_r
+    monkeypatch.setattr(coeffs, "choose_r", lambda eps, ratio, r_max=40: orig(eps, ratio, r_max) + 1)
+    import test_oracle_coeffs as t_coeffs
+    fails(t_coeffs.test_r_matches_paper_value)
+
+
+def test_taylor_coefficients_instead_of_the_best_approximation(monkeypatch):
+    import math
+    import test_oracle_coeffs as t_coeffs
+
+    def taylor(xi, r):
+        w = np.array([(1j * math.pi) ** j / math.factorial(j) for j in range(r)])
+        return w, coeffs.uniform_error(w, xi)
+    monkeypatch.setattr(coeffs, "best_approximation", taylor)
+    fails(t_coeffs.test_best_error_between_bessel_bounds, 8, 1.0)

@@ -145,6 +145,22 @@ def test_noise_free_recovery_up_to_global_phase():
     assert pie.relative_error(z[mask], obj[mask]) >= errs[-1] - 1e-15
 
 
+def test_error_metrics_closed_forms():
+    """Section 4's stopping rule divides by the previous iterate:
+    ||2x - x|| / ||x|| = 1 (0.5 against the new one). The phase-aligned error
+    of a rotated, scaled copy is |1 - s| whatever the phase, and it only sees
+    the masked pixels."""
+    x = _rand((12, 12), 14)
+    assert pie.relative_change(2 * x, x) == pytest.approx(1.0, rel=1e-14)
+    assert pie.nrmse(0.75 * np.exp(-2.1j) * x, x) == pytest.approx(0.25, rel=1e-12)
+    y = x.copy()
+    mask = np.zeros(x.shape, bool)
+    mask[2:8, 3:9] = True
+    y[~mask] += 5.0
+    assert pie.nrmse(np.exp(0.4j) * y, x, mask) == pytest.approx(0.0, abs=1e-14)
+    assert pie.relative_error(np.exp(0.4j) * x, x) == pytest.approx(abs(np.exp(0.4j) - 1), rel=1e-12)
+
+
 def test_hybrid_runs_both_phases_and_stops_on_tolerance():
     """Algorithm 3: PFT sweeps on cropped data, then FULL sweeps; each phase
     stops on its relative-change tolerance or its sweep budget."""
