@@ -518,11 +518,11 @@ def _csrc_sha(name: str) -> str:
 # the sources they were taken on.
 PIE_TRAFFIC = {
     "pie_pft": {"sources": {"pie_kernels.cuh": "5d6bcd1816b610f3d9629d66a063d2cbbd41d4ed67602f2e833a9df6637209a7",
-                            "pft_core.cuh": "8e1db7fdcbf044cf493f01e80163628327931b8efe774c64fd96074c7f8ea072",
+                            "pft_core.cuh": "4dfa31346e0ac684953fa89ce8271d10337e260a8ecc858bb0f8b85d03925495",
                             "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
                 "read_per_position": 529920 / 128, "write_per_position": 1408768 / 128},
     "pie_full": {"sources": {"pie_kernels.cuh": "5d6bcd1816b610f3d9629d66a063d2cbbd41d4ed67602f2e833a9df6637209a7",
-                             "fft_core.cuh": "09cb4b087056aa59c79069c8ed564712ebff83ebb98a195e5682d47eb335d05e",
+                             "fft_core.cuh": "dd2552f57edd2220bfec6952833eeb81f9edcb4dd2d2b1e7f4bd407c1bbe064a",
                              "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
                  "read_per_position": 8501248 / 128, "write_per_position": 56576 / 128},
 }

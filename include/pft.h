@@ -94,7 +94,7 @@ int pft_version(void);
  *   real values a_0..a_{r-1} to a[] (host array of length >= r), and the
  *   uniform error of the polynomial on |x| <= xi to *err (may be NULL).
  *   1 <= r <= 32, 0 < eps < 1. Thread-safe; results are cached.
- * pft_choose_r: Algorithm 1 step 2, r = min{ r : xi(eps, r) >= ratio },
+ * pft_choose_r: the choice of r in Algorithm 1, r = min{ r : xi(eps, r) >= ratio },
  *   ratio = m~/p = M/(2p). Writes r to *r (INVALID_ARG if none <= 32).
  */
 int pft_design_coefficients(double eps, int r, double* xi, double* a, double* err);
@@ -186,7 +186,7 @@ int pft_fft_crop(const void* in, void* out, int n, int M, int64_t batch, void* s
  *                0 <= row <= obj_h - n, 0 <= col <= obj_w - n;
  *   intensities: device float [N][n][n], far-field intensities in FFT order
  *                (not shifted). The context stores d = sqrt(I) and the
- *                centred crop d^crop (Algorithm 3, step 1).
+ *                centred crop d^crop (the cropped data of Algorithm 3).
  *   Synchronises `stream` once. The caller's buffers may be freed afterwards.
  */
 typedef struct pie_ctx pie_ctx;

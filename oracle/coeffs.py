@@ -175,7 +175,7 @@ def coefficients(eps: float, r: int) -> tuple[float, np.ndarray]:
 
 
 def choose_r(eps: float, ratio: float, r_max: int = 40) -> int:
-    """r = min{ r : xi(eps, r) >= ratio }, ratio = m~ / p (Algorithm 1, step 2).
+    """r = min{ r : xi(eps, r) >= ratio }, ratio = m~ / p (the choice of r in Algorithm 1).
 
     Since the best error grows with xi, xi(eps, r) >= ratio exactly when the
     best approximation on |x| <= ratio already meets eps.

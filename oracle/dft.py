@@ -66,7 +66,7 @@ def fft_then_crop(z: np.ndarray, M1: int, M2: int) -> np.ndarray:
 def crop_centre(d: np.ndarray, M1: int, M2: int) -> np.ndarray:
     """d^crop: the centred M1 x M2 block of FFT-ordered data d[..., n1, n2].
 
-    Algorithm 3, step 1 crops the centres of the (shifted) data; with data in
+    Algorithm 3 crops the centres of the (shifted) data; with data in
     FFT order this is d^crop[t1 + M1/2, t2 + M2/2] = d[t1 mod n1, t2 mod n2].
     """
     n1, n2 = d.shape[-2:]

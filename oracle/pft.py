@@ -1,6 +1,6 @@
 """Online phase of the PFT (Algorithms 2 and 5) and the adjoint of Algorithm 5.
 
-1-D (Algorithm 2), with the Algorithm-1 tables B (q x r) and W (M x r):
+1-D (Algorithm 2), with the tables of Algorithm 1, B (q x r) and W (M x r):
     Z = z.reshape(p, q);  C = Z B;  C^[:, j] = FFT_p(C[:, j]);
     z^_PFT[t] = sum_j C^[t mod p, j] W[t, j].
 
@@ -26,11 +26,11 @@ import numpy as np
 def pft1(z: np.ndarray, plan: dict) -> np.ndarray:
     """Algorithm 2 on a vector z (length n); returns M values for t = -M/2 .. M/2-1."""
     p, q, t = plan["p"], plan["q"], plan["t"]
-    Z = z.reshape(p, q)                       # step 1
-    C = Z @ plan["B"]                         # step 2
-    Chat = np.fft.fft(C, axis=0)              # steps 3-4, FFT of each column
+    Z = z.reshape(p, q)                       # p blocks of q consecutive values
+    C = Z @ plan["B"]                         # compress every block with B
+    Chat = np.fft.fft(C, axis=0)              # length-p FFT of each column
     out = np.zeros(t.size, dtype=np.complex128)
-    for a, tt in enumerate(t):                # steps 5-6
+    for a, tt in enumerate(t):                # combine with W at residue t mod p
         out[a] = np.sum(Chat[tt % p, :] * plan["W"][a, :])
     return out
 
@@ -53,14 +53,14 @@ def _pft2_frames(z: np.ndarray, plan1: dict, plan2: dict) -> np.ndarray:
     p2, q2 = plan2["p"], plan2["q"]
     B1, B2, W1, W2 = plan1["B"], plan2["B"], plan1["W"], plan2["W"]
     lead = z.shape[:-2]
-    Z = z.reshape(*lead, p1, q1, p2, q2)                      # step 1
-    Z = np.moveaxis(Z, -3, -2)                                # steps 2-3 -> [.., p1, p2, q1, q2]
-    # steps 4-5: C[k1, k2] = B1^T Z[k1, k2] B2 for every block (k1, k2)
+    Z = z.reshape(*lead, p1, q1, p2, q2)                      # blocks of q1 x q2
+    Z = np.moveaxis(Z, -3, -2)                                # -> [.., p1, p2, q1, q2]
+    # compression: C[k1, k2] = B1^T Z[k1, k2] B2 for every block (k1, k2)
     C = np.einsum("lj,...abls,sk->...abjk", B1, Z, B2, optimize=True)
-    Chat = np.fft.fft2(C, axes=(-4, -3))                      # steps 6-7
+    Chat = np.fft.fft2(C, axes=(-4, -3))                      # p1 x p2 FFT per (j1, j2)
     t1, t2 = plan1["t"], plan2["t"]
     G = Chat[..., np.mod(t1, p1), :, :, :][..., np.mod(t2, p2), :, :]   # [.., M1, M2, r1, r2]
-    return np.einsum("...abjk,aj,bk->...ab", G, W1, W2, optimize=True)  # steps 8-9
+    return np.einsum("...abjk,aj,bk->...ab", G, W1, W2, optimize=True)  # combine with W1, W2
 
 
 def pft2_adjoint(y: np.ndarray, plan1: dict, plan2: dict, chunk: int = 16) -> np.ndarray:
@@ -79,15 +79,15 @@ def _pft2_adjoint_frames(y: np.ndarray, plan1: dict, plan2: dict) -> np.ndarray:
     B1, B2, W1, W2 = plan1["B"], plan2["B"], plan1["W"], plan2["W"]
     t1, t2 = plan1["t"], plan2["t"]
     lead = y.shape[:-2]
-    # adjoint of steps 8-9: G[t1, t2, j1, j2] = conj(W1) conj(W2) y, summed by residue
+    # adjoint of the W combine: G[t1, t2, j1, j2] = conj(W1) conj(W2) y, summed by residue
     G = np.einsum("...ab,aj,bk->...abjk", y, W1.conj(), W2.conj(), optimize=True)
     H = np.zeros((*lead, p1, p2, r1, r2), dtype=np.complex128)
     for a, u1 in enumerate(np.mod(t1, p1)):
         for b, u2 in enumerate(np.mod(t2, p2)):
             H[..., u1, u2, :, :] += G[..., a, b, :, :]
-    # adjoint of steps 6-7: the unnormalised DFT's adjoint is p1 p2 * inverse DFT
+    # adjoint of the p1 x p2 FFT: the unnormalised DFT's adjoint is p1 p2 * inverse DFT
     E = np.fft.ifft2(H, axes=(-4, -3)) * (p1 * p2)
-    # adjoint of steps 4-5: Z[k1, k2] = conj(B1) E[k1, k2] B2^H
+    # adjoint of the compression: Z[k1, k2] = conj(B1) E[k1, k2] B2^H
     Z = np.einsum("lj,...abjk,sk->...abls", B1.conj(), E, B2.conj(), optimize=True)
-    # adjoint of steps 1-3 (a permutation): back to [n1, n2]
+    # adjoint of the blocking (a permutation): back to [n1, n2]
     return np.moveaxis(Z, -2, -3).reshape(*lead, p1 * q1, p2 * q2)

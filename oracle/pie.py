@@ -61,7 +61,7 @@ def partial_dft_transform(n1: int, n2: int, M1: int, M2: int) -> dict:
 
 
 def amplitudes(intensities: np.ndarray, M: int | None = None) -> np.ndarray:
-    """d_j = sqrt(I_j) (FFT order); with M, the centred crop d_j^crop (Alg. 3 step 1)."""
+    """d_j = sqrt(I_j) (FFT order); with M, the centred crop d_j^crop (the cropped data of Algorithm 3)."""
     d = np.sqrt(np.maximum(np.asarray(intensities, dtype=np.float64), 0.0))
     return d if M is None else _dft.crop_centre(d, M, M)
 
@@ -252,7 +252,7 @@ def hybrid_pie(init: np.ndarray, probe: np.ndarray, positions: np.ndarray,
     """
     n1, n2 = probe.shape
     d_full = amplitudes(intensities)
-    d_crop = _dft.crop_centre(d_full, M, M)                  # step 1
+    d_crop = _dft.crop_centre(d_full, M, M)                  # cropped data for the PFT phase
     T_full = full_transform(n1, n2)
     mask = illuminated_mask(probe, positions, init.shape) if truth is not None else None
     z = np.array(init, dtype=np.complex128, copy=True)
@@ -260,7 +260,7 @@ def hybrid_pie(init: np.ndarray, probe: np.ndarray, positions: np.ndarray,
     from . import tv as _tv
     for phase, T, data, beta, tol, mx, lam in (("pft", T_pft, d_crop, beta_pft, tol_pft, max_pft, tv_pft),
                                                 ("full", T_full, d_full, beta_full, tol_full, max_full, tv_full)):
-        for _ in range(mx):                                  # steps 2 and 3
+        for _ in range(mx):                                  # the PFT phase, then the full phase
             z_new, phi = pie_sweep(z, probe, positions, data, T, beta, order)
             if lam > 0.0:
                 z_new = _tv.tv_step(z_new, lam, tv_eps)

@@ -11,7 +11,7 @@ bool design(double eps, int r, double* xi, double* a, double* err);
 // Uniform error of the designed polynomial with r terms on |x| <= X.
 double design_error(double X, int r);
 
-// Algorithm 1, step 2: min{ r : xi(eps, r) >= ratio }, or -1.
+// The choice of r in Algorithm 1: min{ r : xi(eps, r) >= ratio }, or -1.
 int choose_r(double eps, double ratio);
 
 }  // namespace pftc

@@ -1,6 +1,7 @@
 // N-point FFTs on one warp (N = L * E: L lanes, min(N, 32) by default, E values
 // per lane), the building block of the full 2-D transform used by the refine
-// phase of the hybrid (Algorithm 3, step 3) and by the FFT-then-crop baseline.
+// phase of the hybrid (the full-FFT phase of Algorithm 3) and by the FFT-then-crop
+// baseline.
 //
 // A row held as x[e] = v[lane + L e] is transformed in three steps:
 //   1. an E-point DFT over e in registers,

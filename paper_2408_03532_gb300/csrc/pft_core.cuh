@@ -6,13 +6,13 @@
 //
 // One 1-D transform of a length-n vector (n = P Q) runs on a group of P lanes
 // of a warp; lane k owns the block x[Q k .. Q k + Q - 1]:
-//   stage A (Algorithm 2 line 2, C = Z B): C[k][j] = sum_l B[l][j] x[Q k + l],
+//   stage A of Algorithm 2 (the compression C = Z B): C[k][j] = sum_l B[l][j] x[Q k + l],
 //     with B[l][j] = a_j (1 - 2 l / Q)^j real. Rows l and Q - l have opposite
 //     abscissae, so even j use x_l + x_{Q-l} and odd j use x_l - x_{Q-l},
 //     halving the multiply-adds. B sits in the kernel's parameter space and
 //     every index is a compile-time constant, so it is read as a constant
 //     operand of the FMA instructions.
-//   stage B (lines 3-6): a P-point DFT over k for each j, done across the P
+//   stage B of Algorithm 2 (the expansion): a P-point DFT over k for each j, across the P
 //     lanes by a radix-2 butterfly network with shuffles and per-lane register
 //     twiddles (lane k then holds residue v = bitrev(k)), followed by
 //     z^[t] = sum_j W'[t][j] C^[t mod P][j] for the M/P outputs t = v mod P,
