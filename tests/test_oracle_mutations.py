@@ -294,3 +294,61 @@ def test_taylor_coefficients_instead_of_the_best_approximation(monkeypatch):
         return w, coeffs.uniform_error(w, xi)
     monkeypatch.setattr(coeffs, "best_approximation", taylor)
     fails(t_coeffs.test_best_error_between_bessel_bounds, 8, 1.0)
+
+
+# ---------------------------------------------------------------- data, blind PIE, probe gradient
+def test_crop_one_frequency_off(monkeypatch):
+    def bad(d, M1, M2):
+        n1, n2 = d.shape[-2:]
+        i1 = np.mod(coeffs.freqs(M1) + 1, n1)                               # t + 1 instead of t
+        i2 = np.mod(coeffs.freqs(M2), n2)
+        return d[..., i1, :][..., :, i2]
+    monkeypatch.setattr(dft, "crop_centre", bad)
+    fails(t_dft.test_crop_centre_matches_shifted_crop)
+
+
+def test_amplitudes_without_the_square_root(monkeypatch):
+    monkeypatch.setattr(pie, "amplitudes", lambda I, M=None: np.asarray(I, dtype=np.float64) if M is None
+                        else dft.crop_centre(np.asarray(I, dtype=np.float64), M, M))
+    fails(t_pie.test_truth_is_a_fixed_point_and_phase_invariance)
+
+
+@pytest.mark.parametrize("kind", ["conj_probe", "unnormalised"])
+def test_blind_probe_step_with_the_wrong_factor(monkeypatch, kind):
+    def bad(obj, probe, positions, data, T, beta, gamma, colours, order=None, delta_rel=1e-3):
+        n1, n2 = probe.shape
+        z = np.array(obj, dtype=np.complex128, copy=True)
+        w = np.array(probe, dtype=np.complex128, copy=True)
+        cm = pie.colour_major_order(colours, order)
+        tot = 0.0
+        for c in range(int(colours.max()) + 1):
+            members = [j for j in cm if colours[j] == c]
+            wmax2 = float(np.max(np.abs(w) ** 2))
+            for j in members:
+                tot += pie.pie_update(z, w, positions[j], data[j], T, beta, wmax2)
+            acc, den = np.zeros_like(w), np.zeros(w.shape)
+            for j in members:
+                r, cc = positions[j]
+                zj = z[r:r + n1, cc:cc + n2]
+                R = pie.residual(T["fwd"](w * zj), data[j])
+                acc += (np.conj(w) if kind == "conj_probe" else np.conj(zj)) * T["adj"](R) / (n1 * n2)
+                den += np.abs(zj) ** 2
+            w = w - gamma * acc / ((den + delta_rel * den.max()) if kind == "conj_probe" else 1.0)
+        return z, w, tot / len(positions)
+    monkeypatch.setattr(pie, "epie_colour_sweep", bad)
+    fails(t_pie.test_epie_single_position_probe_step)
+
+
+def test_probe_gradient_without_the_conjugate_patch(monkeypatch):
+    orig = grad.amplitude_loss_grad
+
+    def bad(z, probe, positions, d, T):
+        n1, n2 = probe.shape
+        loss, gz, _ = orig(z, probe, positions, d, T)
+        P = np.stack([z[r:r + n1, c:c + n2] for r, c in positions])
+        Psi = T["fwd"](probe[None] * P)
+        mag = np.abs(Psi)
+        R = Psi - d * np.where(mag > 0.0, Psi / np.where(mag > 0.0, mag, 1.0), 0.0)
+        return loss, gz, np.sum(P * 2.0 * T["adj"](R), axis=0)              # Q_j z instead of conj(Q_j z)
+    monkeypatch.setattr(grad, "amplitude_loss_grad", bad)
+    fails(_gradient_pin, *_small_gradient_problem())
