@@ -67,3 +67,51 @@ def test_binding_refuses_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pft, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         pft.load()
+
+
+def test_null_and_invalid_arguments_are_refused_before_any_gpu_work(lib):
+    """Every entry point checks its arguments first: NULL handles, NULL outputs
+    and impossible values return PFT_ERR_INVALID_ARG (-1) with a message, on a
+    machine without a GPU as on one with."""
+    null = None
+    out = ctypes.c_void_p()
+    calls = [
+        lambda: lib.pft_plan_create(null, 64, 64, 32, 32, 0, 0, 1e-7, 0, 0, 0, 0),
+        lambda: lib.pft_plan_create(ctypes.byref(out), 64, 64, 32, 32, 0, 0, 2.0, 0, 0, 0, 0),  # eps >= 1
+        lambda: lib.pft_plan_info_get(null, null),
+        lambda: lib.pft_forward(null, null, null, 1, null),
+        lambda: lib.pft_adjoint(null, null, null, 1, null),
+        lambda: lib.pft_fft2(null, null, 64, 1, 0, null),
+        lambda: lib.pft_fft_crop(null, null, 64, 32, -1, null),
+        lambda: lib.pie_ctx_info_get(null, null),
+        lambda: lib.pie_ctx_colours(null, null, null),
+        lambda: lib.pie_iteration(null, null, 0, 1.0, null, null),
+        lambda: lib.pie_ctx_set_persistent(null, 0, 1),
+        lambda: lib.pie_ctx_set_order(null, null),
+        lambda: lib.pie_nrmse(null, null, null, null, null),
+        lambda: lib.pie_amp_loss_grad(null, null, null, null, null, null, null),
+        lambda: lib.pie_batch_create(ctypes.byref(out), 0, null, null, null, null, null),
+        lambda: lib.pie_batch_iteration(null, null, 0, 1.0, null, null),
+        lambda: lib.pie_batch_classes(null, null, null),
+        lambda: lib.pie_batch_set_launch(null, 0),
+    ]
+    for i, call in enumerate(calls):
+        assert call() == -1, i
+        assert lib.pft_last_error(), i
+
+
+def test_scan_schedule_argument_checks(lib):
+    pos = np.zeros((2, 2), np.int32)
+    ncol, ndep = ctypes.c_int(), ctypes.c_int64()
+    dep = np.zeros(0, np.int32)
+    ok = lib.pie_scan_schedule(pos.ctypes.data, 2, 16, 32, 32, None, ctypes.byref(ncol), None, None, None, None, 0,
+                               ctypes.byref(ndep))
+    assert ok == 0 and ncol.value == 2 and ndep.value == 1
+    # a dep buffer too small for the lists is refused, with the count still reported
+    assert lib.pie_scan_schedule(pos.ctypes.data, 2, 16, 32, 32, None, ctypes.byref(ncol), None, None, None,
+                                 dep.ctypes.data, 0, ctypes.byref(ndep)) == -1
+    assert ndep.value == 1 and b"needed" in lib.pft_last_error()
+    assert lib.pie_scan_schedule(None, 2, 16, 32, 32, None, ctypes.byref(ncol), None, None, None, None, 0,
+                                 ctypes.byref(ndep)) == -1
+    assert lib.pie_scan_schedule(pos.ctypes.data, 2, 40, 32, 32, None, ctypes.byref(ncol), None, None, None, None,
+                                 0, ctypes.byref(ndep)) == -1                 # patch larger than the object
