@@ -412,24 +412,36 @@ int pie_batch_classes(const pie_batch* batch, int* nclasses, int* launches_per_s
 int pie_batch_set_launch(pie_batch* batch, int form);
 
 /* ---- allocation-free error reduction ------------------------------------
- * The paper has no counterpart to this call; it exists for callers that cannot
- * allocate device memory when they need the error: code being recorded into a
- * CUDA graph (cudaMalloc / cudaFree are not allowed during stream capture),
- * latency-critical loops (allocation can synchronise the whole device), and
- * plug-ins in a host framework that owns every device allocation.
+ * The paper has no counterpart to this call. It exists for callers that cannot
+ * call cudaMalloc when they need the error: plug-ins inside a host framework
+ * that owns every device allocation through its own pool (an allocation made
+ * behind the pool's back breaks its accounting or is refused), and
+ * latency-critical loops, where cudaMalloc / cudaFree can synchronise the
+ * whole device.
  *
  * pie_nrmse_noalloc(object, truth, mask, count, out, stream)
  *   Same quantity as pie_nrmse, min_phi ||e^{i phi} z - truth|| / ||truth||,
  *   over the elements whose mask byte is non-zero (mask == NULL: all).
  *   object, truth: device complex [count]; mask: device uint8 [count] or NULL;
  *   out: host double. 1 <= count <= 16,777,216 (a 4096 x 4096 object); larger
- *   counts return PFT_ERR_INVALID_ARG. Synchronises `stream`.
- *   It calls no allocator: its partial sums live in a fixed 128 KiB array
- *   compiled into the library (held on every GPU that loads the library until
- *   the process exits). The first call on a device looks up that array's
- *   device address, so make that first call before any stream capture. All
- *   calls share the array: calls that overlap on the GPU (other streams, other
- *   host threads) race and must be serialised by the caller.
+ *   counts return PFT_ERR_INVALID_ARG before any GPU work. Two passes on the
+ *   device (the aligning phase, then the sum of |e^{i phi} z - truth|^2), then
+ *   the call copies the result to the host and synchronises `stream`.
+ *   It calls no allocator (no cudaMalloc, no cudaFree, no library routine that
+ *   allocates): its partial sums live in a fixed 128 KiB array compiled into
+ *   the library, held on every GPU that loads the library until the process
+ *   exits.
+ *   Set-up: the first call on a device, with that device current, looks up the
+ *   array's device address (cudaGetSymbolAddress, which can load the library's
+ *   device code on that device) and keeps it; make that first call before any
+ *   stream capture begins, since the lookup is a CUDA call that a capture in
+ *   progress may refuse (the call then returns PFT_ERR_CUDA). The kept address
+ *   is not refreshed after cudaDeviceReset; do not use the call on a device
+ *   after resetting it.
+ *   All calls share the array and each call leaves its sums in it; every slot a
+ *   call reads is written earlier by the same call. Calls that overlap on the
+ *   GPU (other streams, other host threads) race on the array and must be
+ *   serialised by the caller.
  */
 int pie_nrmse_noalloc(const void* object, const void* truth, const uint8_t* mask, int64_t count,
                       double* out, void* stream);

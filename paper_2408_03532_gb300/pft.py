@@ -259,9 +259,11 @@ def fft_crop(x, M: int, out=None, stream=None):
 def nrmse_noalloc(obj, truth, mask=None, stream=None) -> float:
     """Phase-aligned error of obj against truth over mask (uint8, or None for
     all elements), computed without any device allocation: for callers that
-    cannot allocate at that moment (inside stream capture, in latency-critical
-    loops, or under a framework that owns all device memory). The library keeps
-    the partial sums in one fixed device array, so calls must not overlap."""
+    cannot call cudaMalloc when they need the error (a framework that owns all
+    device memory through its own pool, or a latency-critical loop where an
+    allocation can synchronise the device). The library keeps the partial sums
+    in one fixed device array, so calls must not overlap on the GPU; the call
+    synchronises its stream before returning."""
     import torch
     _need(obj, torch.complex64, None, "obj")
     _need(truth, torch.complex64, tuple(obj.shape), "truth")
