@@ -131,20 +131,52 @@ def illumination(probe: np.ndarray, positions: np.ndarray, shape) -> np.ndarray:
     return out
 
 
+def epie_sweep(obj: np.ndarray, probe: np.ndarray, positions: np.ndarray, data: np.ndarray,
+               T: dict, beta: float, gamma: float, order=None) -> tuple[np.ndarray, np.ndarray, float]:
+    """Blind PIE as Section 2.1 states it: one sweep of Eq. pie_update and Eq.
+    epie_probe_update, the probe refined after every position.
+
+    Positions are visited in ``order`` (index order by default; the blind
+    experiments of Section 4.2 draw a uniformly random order without
+    replacement). At position j, with the current probe w^k:
+      1. z_j^{k+1} = z_j^k - beta conj(w^k)/max|w^k|^2 (w^k z_j^k - P_M(z_j^k))
+         (the object step with reading R8's normalisation);
+      2. w^{k+1} = w^k - gamma conj(z_j^{k+1}) (w^k z_j^{k+1} - P_M(z_j^{k+1})),
+         the projection taken with w^k (the modulus set of Eq. epie_probe_update
+         is the one of w^k) and gamma a plain scalar, as printed.
+    w z - P_M(z) is A^H R / (n1 n2) (reading R4). Returns (z, w, Phi), Phi from
+    the object steps."""
+    n1, n2 = probe.shape
+    z = np.array(obj, dtype=np.complex128, copy=True)
+    w = np.array(probe, dtype=np.complex128, copy=True)
+    order = range(len(positions)) if order is None else order
+    tot = 0.0
+    for j in order:
+        tot += pie_update(z, w, positions[j], data[j], T, beta, float(np.max(np.abs(w) ** 2)))
+        r, c = int(positions[j][0]), int(positions[j][1])
+        zj = z[r:r + n1, c:c + n2]                       # z_j^{k+1}
+        R = residual(T["fwd"](w * zj), data[j])
+        w = w - gamma * np.conj(zj) * (T["adj"](R) / (n1 * n2))
+    return z, w, tot / len(positions)
+
+
 def epie_colour_sweep(obj: np.ndarray, probe: np.ndarray, positions: np.ndarray, data: np.ndarray,
                       T: dict, beta: float, gamma: float, colours: np.ndarray, order=None,
-                      delta_rel: float = 1e-3) -> tuple[np.ndarray, np.ndarray, float]:
-    """Blind PIE (Eq. pie_update and Eq. epie_probe_update), colour-synchronous.
+                      delta_rel: float = 1e-3, normalise: bool = True) -> tuple[np.ndarray, np.ndarray, float]:
+    """Blind PIE, colour-synchronous: a parallel variant of epie_sweep (reading R14).
 
-    Reading: the probe is shared by every position, so positions that run
-    together cannot each see the probe left by the previous one. Within a colour
-    every position uses the probe w of the colour's start and updates its patch
-    (Eq. pie_update); then the probe step of Eq. epie_probe_update is evaluated at
-    the updated patch z_j^{k+1},
+    The probe is shared by every position, so positions that run together
+    cannot each see the probe left by the previous one. Within a colour every
+    position uses the probe w of the colour's start and updates its patch
+    (Eq. pie_update); then the probe step of Eq. epie_probe_update is evaluated
+    at the updated patch z_j^{k+1},
         g_j = conj(z_j^{k+1}) . (w . z_j^{k+1} - P_M(z_j^{k+1})),
-    and the colour's steps are summed and normalised pixel by pixel:
+    and the colour's steps are summed. With ``normalise`` (the default) the sum
+    is divided pixel by pixel,
         w <- w - gamma * sum_j g_j / (sum_j |z_j^{k+1}|^2 + delta),
-    delta = delta_rel * max of that sum. Returns (z, w, Phi)."""
+    delta = delta_rel * max of that sum; without it w <- w - gamma sum_j g_j,
+    the scalar step of Eq. epie_probe_update, and with one position per colour
+    the sweep is then epie_sweep in colour-major order. Returns (z, w, Phi)."""
     n1, n2 = probe.shape
     z = np.array(obj, dtype=np.complex128, copy=True)
     w = np.array(probe, dtype=np.complex128, copy=True)
@@ -163,8 +195,17 @@ def epie_colour_sweep(obj: np.ndarray, probe: np.ndarray, positions: np.ndarray,
             R = residual(T["fwd"](w * zj), data[j])
             acc += np.conj(zj) * T["adj"](R) / (n1 * n2)
             den += np.abs(zj) ** 2
-        w = w - gamma * acc / (den + delta_rel * den.max())
+        w = w - gamma * (acc / (den + delta_rel * den.max()) if normalise else acc)
     return z, w, tot / len(positions)
+
+
+def sequential_colouring(order) -> np.ndarray:
+    """One position per colour, colours in visiting order: colour-major order
+    is then the visiting order itself (exact sequential PIE)."""
+    order = np.asarray(order)
+    col = np.empty(len(order), dtype=np.int64)
+    col[order] = np.arange(len(order))
+    return col
 
 
 # ---------------------------------------------------------------------------

@@ -352,3 +352,40 @@ def test_probe_gradient_without_the_conjugate_patch(monkeypatch):
         return loss, gz, np.sum(P * 2.0 * T["adj"](R), axis=0)              # Q_j z instead of conj(Q_j z)
     monkeypatch.setattr(grad, "amplitude_loss_grad", bad)
     fails(_gradient_pin, *_small_gradient_problem())
+
+
+# ---------------------------------------------------------------- Eq. epie_probe_update, sequential
+def _bad_epie_sweep(kind):
+    def bad(obj, probe, positions, data, T, beta, gamma, order=None):
+        n1, n2 = probe.shape
+        z = np.array(obj, dtype=np.complex128, copy=True)
+        w = np.array(probe, dtype=np.complex128, copy=True)
+        order = range(len(positions)) if order is None else order
+        acc = np.zeros_like(w)
+        tot = 0.0
+        for j in order:
+            r, c = int(positions[j][0]), int(positions[j][1])
+            zold = z[r:r + n1, c:c + n2].copy()
+            tot += pie.pie_update(z, w, positions[j], data[j], T, beta, float(np.max(np.abs(w) ** 2)))
+            zj = zold if kind == "old_patch" else z[r:r + n1, c:c + n2]
+            R = pie.residual(T["fwd"](w * zj), data[j])
+            g = (zj if kind == "no_conj" else np.conj(zj)) * (T["adj"](R) / (n1 * n2))
+            if kind == "summed":
+                acc += g                                                      # one step at the end of the sweep
+            else:
+                w = w + gamma * g if kind == "uphill" else w - gamma * g
+        if kind == "summed":
+            w = w - gamma * acc
+        return z, w, tot / len(positions)
+    return bad
+
+
+@pytest.mark.parametrize("kind,pin", [
+    ("old_patch", "test_epie_sweep_probe_step_at_the_updated_patch"),
+    ("no_conj", "test_epie_sweep_probe_step_projects_the_probe"),
+    ("uphill", "test_epie_sweep_probe_step_projects_the_probe"),
+    ("summed", "test_epie_sweep_updates_the_probe_after_every_position"),
+])
+def test_epie_sweep_mistakes(monkeypatch, kind, pin):
+    monkeypatch.setattr(pie, "epie_sweep", _bad_epie_sweep(kind))
+    fails(getattr(t_pie, pin))

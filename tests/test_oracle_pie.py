@@ -242,3 +242,82 @@ def test_epie_fits_the_data_up_to_blind_ambiguities():
         phis.append(phi)
     assert phis[-1] < 0.1 * phis[0]
     assert exit_err(z, w) < 0.25 * e0
+
+
+# ---------------------------------------------------------------- Eq. epie_probe_update, sequential
+def test_epie_sweep_probe_step_projects_the_probe():
+    """One position, beta = 0 (the patch stays c, a non-real unit constant),
+    gamma = 1: Eq. epie_probe_update gives w' = w - conj(c)(c w - P_M) =
+    conj(c) P_M, so the new exit wave c w' has spectrum d e^{i theta(F(c w))}:
+    modulus d and the phase of the old exit wave's spectrum."""
+    n = 16
+    c = np.exp(0.9j)
+    obj = np.full((24, 24), c)
+    w = _rand((n, n), 21)
+    d = np.random.default_rng(22).random((1, n, n)) + 0.1
+    pos = np.array([[4, 3]], dtype=np.int32)
+    z, w1, _ = pie.epie_sweep(obj, w, pos, d, pie.full_transform(n, n), 0.0, 1.0)
+    assert np.array_equal(z, obj)
+    old = np.fft.fft2(c * w)
+    assert np.allclose(np.fft.fft2(c * w1), d[0] * old / np.abs(old), rtol=1e-12, atol=1e-12)
+
+
+def test_epie_sweep_probe_step_at_the_updated_patch():
+    """One position, beta = 1, a unit-modulus probe: the object step alone makes
+    the exit wave P_M (w z' = |w|^2 P_M = P_M), so the probe step, evaluated at
+    the updated patch z', has a zero residual and leaves the probe unchanged
+    (evaluated at the old patch it would move it)."""
+    n = 16
+    obj = _rand((24, 24), 23)
+    w = np.exp(2j * np.pi * np.random.default_rng(24).random((n, n)))
+    d = np.random.default_rng(25).random((1, n, n)) + 0.1
+    pos = np.array([[2, 6]], dtype=np.int32)
+    z, w1, _ = pie.epie_sweep(obj, w, pos, d, pie.full_transform(n, n), 1.0, 0.7)
+    assert np.allclose(np.abs(np.fft.fft2(w * z[2:2 + n, 6:6 + n])), d[0], rtol=1e-12, atol=1e-12)
+    assert np.allclose(w1, w, rtol=0, atol=1e-12)
+
+
+def test_epie_sweep_updates_the_probe_after_every_position():
+    """Two positions on the same pixels of an all-ones object, beta = 0,
+    gamma = 1/2: each step keeps the phase of F w and averages its modulus with
+    that position's data, |F w| -> (|F w| + d_j)/2, so after the sweep
+    |F w| = |F w0|/4 + d_1/4 + d_2/2 (the second position sees the probe the
+    first one left; a summed or reordered step gives another modulus)."""
+    n = 16
+    obj = np.ones((20, 20), complex)
+    w0 = _rand((n, n), 26)
+    d = np.random.default_rng(27).random((2, n, n)) + 0.1
+    pos = np.array([[1, 2], [1, 2]], dtype=np.int32)
+    _, w2, _ = pie.epie_sweep(obj, w0, pos, d, pie.full_transform(n, n), 0.0, 0.5)
+    F0 = np.fft.fft2(w0)
+    expect = (np.abs(F0) / 4 + d[0] / 4 + d[1] / 2) * F0 / np.abs(F0)
+    assert np.allclose(np.fft.fft2(w2), expect, rtol=1e-12, atol=1e-12)
+
+
+def test_epie_sweep_with_gamma_zero_is_pie():
+    """gamma = 0: the probe never changes and the sweep is Eq. pie_update alone,
+    in the same visiting order."""
+    P = synth.small_raster_problem()
+    d = pie.amplitudes(P["intensities"])
+    order = np.random.default_rng(28).permutation(len(P["pos"]))
+    T = pie.full_transform(32, 32)
+    z, w, phi = pie.epie_sweep(P["init"], P["probe"], P["pos"], d, T, 0.8, 0.0, order)
+    zs, phis = pie.pie_sweep(P["init"], P["probe"], P["pos"], d, T, 0.8, order)
+    assert np.array_equal(w, P["probe"].astype(np.complex128))
+    assert np.allclose(z, zs, rtol=0, atol=1e-13) and phi == pytest.approx(phis, rel=1e-13)
+
+
+def test_colour_sweep_with_one_position_per_colour_is_the_sequential_sweep():
+    """The colour-synchronous variant with the pixel-wise normaliser off and one
+    position per colour is epie_sweep in the same (random) order, exactly."""
+    P = synth.small_raster_problem()
+    d = pie.amplitudes(P["intensities"], 16)
+    order = np.random.default_rng(29).permutation(len(P["pos"]))
+    col = pie.sequential_colouring(order)
+    assert np.array_equal(pie.colour_major_order(col, order), order)
+    T = pie.pft_transform(*coeffs.plan_2d(32, 32, 16, 16, 8, 8))
+    w0 = P["probe"] * (1 + 0.1 * _rand(P["probe"].shape, 30))
+    z1, w1, p1 = pie.epie_sweep(P["init"], w0, P["pos"], d, T, 0.9, 0.05, order)
+    z2, w2, p2 = pie.epie_colour_sweep(P["init"], w0, P["pos"], d, T, 0.9, 0.05, col, order, normalise=False)
+    assert np.allclose(z1, z2, rtol=0, atol=1e-12) and np.allclose(w1, w2, rtol=0, atol=1e-12)
+    assert p1 == pytest.approx(p2, rel=1e-12)
