@@ -79,6 +79,12 @@ extern "C" {
                                     earlier positions whose patches overlap its
                                     own (no barrier between colours)             */
 
+/* Probe step of a blind sweep (pie_iteration_blind). */
+#define PIE_PROBE_STEP_NORMALISED 0  /* gamma sum_j g_j / (sum_j |z_j|^2 + delta),
+                                        pixel by pixel, once per colour         */
+#define PIE_PROBE_STEP_SCALAR     1  /* gamma sum_j g_j: Eq. epie_probe_update's
+                                        plain scalar step                       */
+
 /* Last error message of the calling thread ("" if none). Never NULL. */
 const char* pft_last_error(void);
 
@@ -257,11 +263,13 @@ int pie_ctx_colours(const pie_ctx* ctx, int* ncolours, int32_t* colour_of);
  *            of that set (waiting for the later one covers them).
  * positions: host int32 [npos][2] top-left (row, col), each patch inside the
  * obj_h x obj_w object; order: host int32 [npos] permutation or NULL (index
- * order). *ncolours and *ndep (the number of dep entries) are always written;
+ * order); one_per_colour != 0: every position is its own colour, colour a
+ * being the a-th position visited (the schedule is then the visiting order
+ * itself). *ncolours and *ndep (the number of dep entries) are always written;
  * every other output may be NULL. INVALID_ARG for a patch outside the object,
  * an order that is not a permutation, or dep_capacity < *ndep with dep set. */
 int pie_scan_schedule(const int32_t* positions, int npos, int n, int obj_h, int obj_w, const int32_t* order,
-                      int* ncolours, int32_t* colour, int32_t* sched, int32_t* dep_off, int32_t* dep,
+                      int one_per_colour, int* ncolours, int32_t* colour, int32_t* sched, int32_t* dep_off, int32_t* dep,
                       int64_t dep_capacity, int64_t* ndep);
 
 /* One PIE sweep over all positions (Eq. pie_update with Eq. 3), in place on
@@ -287,9 +295,14 @@ int pie_iteration_mode(pie_ctx* ctx, void* object, int transform, int mode, doub
  * probe step of Eq. epie_probe_update is then evaluated at each updated patch,
  * g_j = conj(z_j) (w z_j - P_M(z_j)) (a second transform pair per position),
  * and after the colour w <- w - gamma sum_j g_j / (sum_j |z_j|^2 + delta),
- * delta = delta_rel max(sum_j |z_j|^2). The object step is
- * beta conj(w) / max|w|^2 with the probe of that colour. */
-int pie_iteration_blind(pie_ctx* ctx, void* object, int transform, double beta, double gamma,
+ * delta = delta_rel max(sum_j |z_j|^2) (probe_step PIE_PROBE_STEP_NORMALISED)
+ * or w <- w - gamma sum_j g_j (PIE_PROBE_STEP_SCALAR). The object step is
+ * beta conj(w) / max|w|^2 with the probe of that colour. With one position per
+ * colour (pie_ctx_set_order with one_per_colour) and the scalar step this is
+ * Eq. pie_update and Eq. epie_probe_update exactly as stated, the probe
+ * refined after every position in the visiting order. INVALID_ARG for
+ * gamma < 0 or an unknown probe_step. */
+int pie_iteration_blind(pie_ctx* ctx, void* object, int transform, double beta, double gamma, int probe_step,
                         pie_stats* stats, void* stream);
 
 /* Copy the context's current probe into `probe_out` (device [n][n] complex),
@@ -334,10 +347,14 @@ int pie_tv_step(pie_ctx* ctx, void* object, double lambda, double eps, void* str
 
 /* Visiting order of the scan positions (the blind experiments of Section 4.2
  * draw a random order without replacement). order: host int32 [N], a
- * permutation of 0..N-1, or NULL for index order. The positions are
- * re-coloured greedily in that order and every sweep then runs colour-major
- * with that order inside each colour. Synchronises the device. */
-int pie_ctx_set_order(pie_ctx* ctx, const int32_t* order);
+ * permutation of 0..N-1, or NULL for index order. With one_per_colour == 0
+ * the positions are re-coloured greedily in that order and every sweep then
+ * runs colour-major with that order inside each colour; with one_per_colour
+ * != 0 every position is its own colour and sweeps visit the positions in
+ * exactly that order (Section 2.1's sequential j; the dataflow launch form
+ * still runs positions whose patches do not overlap at the same time).
+ * Synchronises the device. */
+int pie_ctx_set_order(pie_ctx* ctx, const int32_t* order, int one_per_colour);
 
 /* How coloured sweeps of `transform` are launched (PIE_LAUNCH_*):
  * PIE_LAUNCH_PERSISTENT runs the whole sweep as one cooperative launch (the

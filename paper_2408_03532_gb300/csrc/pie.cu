@@ -176,10 +176,11 @@ __global__ void k_probe_init(const float2* __restrict__ w, int n2, float2* __res
   }
 }
 
-// Blind PIE, end of a colour: w <- w - gamma acc / (den + delta_rel max den),
+// Blind PIE, end of a colour: w <- w - gamma acc / (den + delta_rel max den)
+// (normalised step) or w <- w - gamma acc (scalar step of Eq. epie_probe_update),
 // then the new max |w|^2 and empty accumulators (single block).
 __global__ void k_probe_apply(float2* __restrict__ w, int n2, float2* __restrict__ acc, float* __restrict__ den,
-                              float gamma, float delta_rel, float* __restrict__ scale) {
+                              float gamma, float delta_rel, int normalise, float* __restrict__ scale) {
   __shared__ float red[32];
   __shared__ float dmax;
   float m = 0.f;
@@ -196,7 +197,7 @@ __global__ void k_probe_apply(float2* __restrict__ w, int n2, float2* __restrict
   const float delta = delta_rel * dmax;
   float pm = 0.f;
   for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-    const float s = gamma / (den[i] + delta);
+    const float s = normalise ? gamma / (den[i] + delta) : gamma;
     float2 v = w[i];
     v.x = fmaf(-s, acc[i].x, v.x);
     v.y = fmaf(-s, acc[i].y, v.y);
@@ -283,6 +284,7 @@ struct pie_ctx {
     double gamma;  // < 0: non-blind
     bool stats;
     int mode;      // PIE_MODE_* of the sweep
+    int probe_step;  // PIE_PROBE_STEP_* of a blind sweep
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;
@@ -335,7 +337,7 @@ struct PieSchedule {
 };
 
 void build_schedule(const std::vector<int2>& pos, int n, int H, int W, const std::vector<int>& order,
-                    PieSchedule& out) {
+                    PieSchedule& out, bool one_per_colour = false) {
   const int N = (int)pos.size();
   // positions bucketed by n x n cells: overlapping patches lie in neighbouring cells
   const int cw = (W + n - 1) / n + 1, ch = (H + n - 1) / n + 1;
@@ -364,6 +366,7 @@ void build_schedule(const std::vector<int2>& pos, int n, int H, int W, const std
     });
     int col = 0;
     while (col < ncol && used[col]) ++col;
+    if (one_per_colour) col = ncol;  // exact sequential order: the a-th visited position is colour a
     out.colour[j] = col;
     if (col == ncol) ++ncol;
     cells[(size_t)(p.x / n) * cw + p.y / n].push_back(j);
@@ -402,9 +405,9 @@ void build_schedule(const std::vector<int2>& pos, int n, int H, int W, const std
 }
 
 // The context's colouring and schedule for a visiting order (empty: index order).
-void colour_positions(pie_ctx* c, const std::vector<int>& order = {}) {
+void colour_positions(pie_ctx* c, const std::vector<int>& order = {}, bool one_per_colour = false) {
   PieSchedule sch;
-  build_schedule(c->h_pos, c->n, c->H, c->W, order, sch);
+  build_schedule(c->h_pos, c->n, c->H, c->W, order, sch, one_per_colour);
   c->visit = std::move(sch.visit);
   c->colour = std::move(sch.colour);
   c->col_off = std::move(sch.col_off);
@@ -560,7 +563,7 @@ int launch_pie_persistent(pie_ctx* c, int transform, PieArgs a, cudaStream_t st)
 }
 
 int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st,
-                  double gamma = -1.0, int mode = -1);
+                  double gamma = -1.0, int mode = -1, int probe_step = PIE_PROBE_STEP_NORMALISED);
 
 __global__ void k_fill(float2* __restrict__ z, long long n, float2 v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -851,7 +854,7 @@ int pie_ctx_info_get(const pie_ctx* c, pie_ctx_info* info) {
 }
 
 int pie_scan_schedule(const int32_t* positions, int npos, int n, int obj_h, int obj_w, const int32_t* order,
-                      int* ncolours, int32_t* colour, int32_t* sched, int32_t* dep_off, int32_t* dep,
+                      int one_per_colour, int* ncolours, int32_t* colour, int32_t* sched, int32_t* dep_off, int32_t* dep,
                       int64_t dep_capacity, int64_t* ndep) {
   if (!positions || !ncolours || !ndep) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
   if (npos < 1 || n < 1 || obj_h < n || obj_w < n)
@@ -873,7 +876,7 @@ int pie_scan_schedule(const int32_t* positions, int npos, int n, int obj_h, int 
     }
   }
   PieSchedule sch;
-  build_schedule(pos, n, obj_h, obj_w, ord, sch);
+  build_schedule(pos, n, obj_h, obj_w, ord, sch, one_per_colour != 0);
   *ncolours = sch.ncol;
   *ndep = (int64_t)sch.dep.size();
   if (dep && dep_capacity < (int64_t)sch.dep.size())
@@ -906,7 +909,7 @@ namespace {
 // (or the batched kernel and its update), and with `stats` the FP64 norms and
 // their copy to pinned host memory.
 int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaStream_t st,
-                  double gamma, int mode) {
+                  double gamma, int mode, int probe_step) {
   const long long HW = (long long)c->H * c->W;
   if (mode < 0) mode = c->pb.mode;
   const bool blind = gamma >= 0.0;
@@ -949,7 +952,8 @@ int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stat
       if (rc != PFT_OK) return rc;
       if (blind) {
         k_probe_apply<<<1, 1024, 0, st>>>(c->d_probe, n2i, c->d_pacc, c->d_pden, (float)gamma,
-                                          (float)(c->pb.delta_rel > 0 ? c->pb.delta_rel : 1e-3), c->d_pscale);
+                                          (float)(c->pb.delta_rel > 0 ? c->pb.delta_rel : 1e-3),
+                                          probe_step == PIE_PROBE_STEP_NORMALISED, c->d_pscale);
         PFT_CUDA_TRY(cudaGetLastError());
       }
     }
@@ -974,10 +978,10 @@ int enqueue_sweep(pie_ctx* c, float2* obj, int transform, double beta, bool stat
 
 // Returns the executable graph of a sweep, capturing it on first use.
 int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats, cudaGraphExec_t* out,
-                double gamma, int mode) {
+                double gamma, int mode, int probe_step) {
   for (auto& g : c->graphs)
     if (g.obj == obj && g.transform == transform && g.beta == beta && g.stats == stats && g.gamma == gamma &&
-        g.mode == mode) {
+        g.mode == mode && g.probe_step == probe_step) {
       *out = g.exec;
       return PFT_OK;
     }
@@ -985,7 +989,7 @@ int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats,
   const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
   for (int attempt = 0;; ++attempt) {
     PFT_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_sweep(c, obj, transform, beta, stats, c->cap_stream, gamma, mode);
+    int rc = enqueue_sweep(c, obj, transform, beta, stats, c->cap_stream, gamma, mode, probe_step);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
     if (rc == PFT_OK && e == cudaSuccess) {
@@ -1008,13 +1012,13 @@ int sweep_graph(pie_ctx* c, float2* obj, int transform, double beta, bool stats,
     cudaGraphExecDestroy(c->graphs.front().exec);
     c->graphs.erase(c->graphs.begin());
   }
-  c->graphs.push_back({obj, transform, beta, gamma, stats, mode, exec});
+  c->graphs.push_back({obj, transform, beta, gamma, stats, mode, probe_step, exec});
   *out = exec;
   return PFT_OK;
 }
 
 int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, pie_stats* stats, void* stream,
-            int mode = -1) {
+            int mode = -1, int probe_step = PIE_PROBE_STEP_NORMALISED) {
   if (!c || !object) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
   if (mode < 0) mode = c->pb.mode;
   if (mode != PIE_MODE_COLOURED && mode != PIE_MODE_BATCHED)
@@ -1041,7 +1045,7 @@ int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, 
     if (!c->d_pscale) PFT_CUDA_TRY(cudaMalloc(&c->d_pscale, sizeof(float)));
   }
   cudaGraphExec_t exec = nullptr;
-  int rc = sweep_graph(c, (float2*)object, transform, beta, stats != nullptr, &exec, gamma, mode);
+  int rc = sweep_graph(c, (float2*)object, transform, beta, stats != nullptr, &exec, gamma, mode, probe_step);
   if (rc != PFT_OK) return rc;
   PFT_CUDA_TRY(cudaGraphLaunch(exec, st));
   if (stats) {
@@ -1068,10 +1072,12 @@ int pie_iteration_mode(pie_ctx* c, void* object, int transform, int mode, double
   return iterate(c, object, transform, beta, -1.0, stats, stream, mode);
 }
 
-int pie_iteration_blind(pie_ctx* c, void* object, int transform, double beta, double gamma, pie_stats* stats,
-                        void* stream) {
+int pie_iteration_blind(pie_ctx* c, void* object, int transform, double beta, double gamma, int probe_step,
+                        pie_stats* stats, void* stream) {
   if (!(gamma >= 0.0)) return pfth::set_error(PFT_ERR_INVALID_ARG, "need gamma >= 0");
-  return iterate(c, object, transform, beta, gamma, stats, stream);
+  if (probe_step != PIE_PROBE_STEP_NORMALISED && probe_step != PIE_PROBE_STEP_SCALAR)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown probe step %d", probe_step);
+  return iterate(c, object, transform, beta, gamma, stats, stream, -1, probe_step);
 }
 
 int pie_ctx_probe(const pie_ctx* c, void* probe_out, void* stream) {
@@ -1132,7 +1138,7 @@ int pie_ctx_set_persistent(pie_ctx* c, int transform, int persistent) {
   return PFT_OK;
 }
 
-int pie_ctx_set_order(pie_ctx* c, const int32_t* order) {
+int pie_ctx_set_order(pie_ctx* c, const int32_t* order, int one_per_colour) {
   if (!c) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
   std::vector<int> ord;
   if (order) {
@@ -1144,7 +1150,7 @@ int pie_ctx_set_order(pie_ctx* c, const int32_t* order) {
     }
   }
   PFT_CUDA_TRY(cudaDeviceSynchronize());  // no sweep of the old schedule may still be running
-  colour_positions(c, ord);
+  colour_positions(c, ord, one_per_colour != 0);
   int rc = upload_schedule(c, nullptr);
   if (rc != PFT_OK) return rc;
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);

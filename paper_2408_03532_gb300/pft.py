@@ -25,6 +25,7 @@ PREC_SPLIT_BF16 = 1
 TRANSFORM_PFT, TRANSFORM_FULL = 0, 1
 MODE_COLOURED, MODE_BATCHED = 0, 1
 LAUNCH_PER_COLOUR, LAUNCH_PERSISTENT, LAUNCH_DATAFLOW = 0, 1, 2
+PROBE_STEP_NORMALISED, PROBE_STEP_SCALAR = 0, 1
 _ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "OOM"}
 
 
@@ -108,13 +109,14 @@ def load() -> ctypes.CDLL:
         "pie_ctx_info_get": (ctypes.c_int, [_P, _P]),
         "pie_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
         "pie_iteration_mode": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P]),
-        "pie_iteration_blind": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P]),
+        "pie_iteration_blind": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                               _P, _P]),
         "pie_ctx_probe": (ctypes.c_int, [_P, _P, _P]),
         "pie_ctx_set_probe": (ctypes.c_int, [_P, _P, _P]),
         "warm_start_then_refine": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse": (ctypes.c_int, [_P, _P, _P, _P, _P]),
         "pie_tv_step": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, _P]),
-        "pie_ctx_set_order": (ctypes.c_int, [_P, _P]),
+        "pie_ctx_set_order": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "pie_ctx_set_persistent": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
         "pie_amp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
@@ -123,8 +125,8 @@ def load() -> ctypes.CDLL:
         "pie_batch_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
         "pie_batch_classes": (ctypes.c_int, [_P, _P, _P]),
         "pie_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int]),
-        "pie_scan_schedule": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
-                                             _P, _P, ctypes.c_int64, _P]),
+        "pie_scan_schedule": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                             ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -278,9 +280,10 @@ def nrmse_noalloc(obj, truth, mask=None, stream=None) -> float:
 
 
 # --------------------------------------------------------------------- PIE
-def pie_scan_schedule(positions, n: int, obj_shape, order=None) -> dict:
+def pie_scan_schedule(positions, n: int, obj_shape, order=None, sequential: bool = False) -> dict:
     """The order a coloured sweep visits the positions in (host only, no GPU):
-    greedy colours, the colour-major schedule and each schedule item's dataflow
+    greedy colours (or, with `sequential`, one colour per position in visiting
+    order), the colour-major schedule and each schedule item's dataflow
     predecessors (schedule indices). Returns a dict with ncolours, colour,
     sched, dep_off and dep (numpy int32 arrays)."""
     lib = load()
@@ -292,11 +295,11 @@ def pie_scan_schedule(positions, n: int, obj_shape, order=None) -> dict:
     h, w = obj_shape
     ncol, ndep = ctypes.c_int(), ctypes.c_int64()
     _check(lib.pie_scan_schedule(pos.ctypes.data, N, int(n), int(h), int(w), None if o is None else o.ctypes.data,
-                                 ctypes.byref(ncol), None, None, None, None, 0, ctypes.byref(ndep)))
+                                 int(sequential), ctypes.byref(ncol), None, None, None, None, 0, ctypes.byref(ndep)))
     colour, sched = np.empty(N, np.int32), np.empty(N, np.int32)
     dep_off, dep = np.empty(N + 1, np.int32), np.empty(max(1, ndep.value), np.int32)
     _check(lib.pie_scan_schedule(pos.ctypes.data, N, int(n), int(h), int(w), None if o is None else o.ctypes.data,
-                                 ctypes.byref(ncol), colour.ctypes.data, sched.ctypes.data, dep_off.ctypes.data,
+                                 int(sequential), ctypes.byref(ncol), colour.ctypes.data, sched.ctypes.data, dep_off.ctypes.data,
                                  dep.ctypes.data, len(dep), ctypes.byref(ndep)))
     return {"ncolours": ncol.value, "colour": colour, "sched": sched, "dep_off": dep_off, "dep": dep[:ndep.value]}
 
@@ -366,15 +369,17 @@ class PieContext:
         self._obj(obj)
         _check(load().pie_tv_step(self._h, _ptr(obj), lam, eps, _stream(stream)))
 
-    def set_order(self, order=None):
-        """Visit the positions in `order` (a permutation; None = index order)."""
+    def set_order(self, order=None, sequential: bool = False):
+        """Visit the positions in `order` (a permutation; None = index order):
+        greedy colours in that order, swept colour-major, or with `sequential`
+        one colour per position, so sweeps follow `order` exactly."""
         if order is None:
-            _check(load().pie_ctx_set_order(self._h, None))
+            _check(load().pie_ctx_set_order(self._h, None, int(sequential)))
             return
         o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
         if o.shape != (self.npos,):
             raise ValueError("order must be a permutation of the positions")
-        _check(load().pie_ctx_set_order(self._h, o.ctypes.data))
+        _check(load().pie_ctx_set_order(self._h, o.ctypes.data, int(sequential)))
 
     def set_persistent(self, transform: int, persistent=True):
         """Launch form of the coloured sweeps of `transform`: LAUNCH_PER_COLOUR
@@ -385,11 +390,13 @@ class PieContext:
         _check(load().pie_ctx_set_persistent(self._h, transform, form))
 
     def iteration_blind(self, obj, transform: int = TRANSFORM_FULL, beta: float = 1.0, gamma: float = 1.0,
-                        stats: bool = True, stream=None):
-        """One blind sweep (object and probe updated; coloured mode)."""
+                        stats: bool = True, stream=None, probe_step: int = 0):
+        """One blind sweep (object and probe updated; coloured mode).
+        probe_step: PROBE_STEP_NORMALISED (pixel-wise, per colour) or
+        PROBE_STEP_SCALAR (Eq. epie_probe_update's scalar gamma)."""
         self._obj(obj)
         st = PieStats()
-        _check(load().pie_iteration_blind(self._h, _ptr(obj), transform, beta, gamma,
+        _check(load().pie_iteration_blind(self._h, _ptr(obj), transform, beta, gamma, int(probe_step),
                                           ctypes.byref(st) if stats else None, _stream(stream)))
         return {"phi": st.phi, "rel_change": st.rel_change} if stats else None
 

@@ -448,3 +448,54 @@ def test_blind_sweeps_match_oracle(env, small, transform):
     assert rel(ctx.probe().cpu().numpy(), wo) < 1e-4
     ctx.set_probe(c64(probe0, torch))
     assert rel(ctx.probe().cpu().numpy(), probe0) == 0.0
+
+
+@pytest.mark.parametrize("transform", ["pft", "full"])
+@pytest.mark.parametrize("form", ["per_colour", "persistent", "dataflow"])
+def test_sequential_order_sweep_matches_oracle(env, small, transform, form):
+    """One colour per position: the sweep visits a seeded random order exactly
+    (Section 2.1's sequential updates in Section 4.2's random order), in every
+    launch form, and matches the oracle's sequential sweep in that order."""
+    torch, pft = env
+    P = small
+    ctx = make_ctx(P, torch, pft)
+    order = np.random.default_rng(31).permutation(len(P["pos"]))
+    ctx.set_order(order, sequential=True)
+    assert np.array_equal(ctx.colours(), opie.sequential_colouring(order))
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    ctx.set_persistent(tr, {"per_colour": pft.LAUNCH_PER_COLOUR, "persistent": pft.LAUNCH_PERSISTENT,
+                            "dataflow": pft.LAUNCH_DATAFLOW}[form])
+    z = c64(P["init"], torch)
+    zo = P["init"].astype(np.complex64).astype(np.complex128)
+    T, d = oracle_T(P, transform)
+    for _ in range(2):
+        phi = ctx.iteration(z, tr, 0.9)["phi"]
+        zo, phio = opie.pie_sweep(zo, P["probe"].astype(np.complex64), P["pos"], d, T, 0.9, order)
+        assert phi == pytest.approx(phio, rel=1e-5)
+    assert rel(z.cpu().numpy(), zo) < TOL
+
+
+@pytest.mark.parametrize("transform", ["pft", "full"])
+def test_blind_paper_order_matches_oracle(env, small, transform):
+    """Eq. pie_update and Eq. epie_probe_update as stated: one position per
+    colour in a seeded random order and the plain scalar probe step, so the
+    probe is refined after every position. Three sweeps of object and probe
+    match the oracle's sequential epie_sweep."""
+    torch, pft = env
+    P = small
+    probe0 = P["probe"] * (1 + 0.2 * np.exp(2j * np.pi * np.random.default_rng(11).random(P["probe"].shape)))
+    probe0 = probe0.astype(np.complex64)
+    ctx = pft.PieContext(P["obj"].shape, c64(probe0, torch), P["pos"],
+                         torch.from_numpy(P["intensities"].astype(np.float32)).cuda(), M=P["M"])
+    order = np.random.default_rng(19).permutation(len(P["pos"]))
+    ctx.set_order(order, sequential=True)
+    z = c64(P["init"], torch)
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    T, d = oracle_T(P, transform)
+    zo, wo = P["init"].astype(np.complex64).astype(np.complex128), probe0.astype(np.complex128)
+    for _ in range(3):
+        phi = ctx.iteration_blind(z, tr, 1.0, 0.2, probe_step=pft.PROBE_STEP_SCALAR)["phi"]
+        zo, wo, phio = opie.epie_sweep(zo, wo, P["pos"], d, T, 1.0, 0.2, order)
+        assert phi == pytest.approx(phio, rel=1e-4)
+    assert rel(z.cpu().numpy(), zo) < 1e-4
+    assert rel(ctx.probe().cpu().numpy(), wo) < 1e-4

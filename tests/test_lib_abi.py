@@ -87,7 +87,10 @@ def test_null_and_invalid_arguments_are_refused_before_any_gpu_work(lib):
         lambda: lib.pie_ctx_colours(null, null, null),
         lambda: lib.pie_iteration(null, null, 0, 1.0, null, null),
         lambda: lib.pie_ctx_set_persistent(null, 0, 1),
-        lambda: lib.pie_ctx_set_order(null, null),
+        lambda: lib.pie_ctx_set_order(null, null, 0),
+        lambda: lib.pie_iteration_blind(null, null, 0, 1.0, 1.0, 0, null, null),
+        lambda: lib.pie_iteration_blind(null, null, 0, 1.0, 1.0, 7, null, null),     # unknown probe step
+        lambda: lib.pie_iteration_blind(null, null, 0, 1.0, -1.0, 1, null, null),    # gamma < 0
         lambda: lib.pie_nrmse(null, null, null, null, null),
         lambda: lib.pie_amp_loss_grad(null, null, null, null, null, null, null),
         lambda: lib.pie_batch_create(ctypes.byref(out), 0, null, null, null, null, null),
@@ -104,14 +107,14 @@ def test_scan_schedule_argument_checks(lib):
     pos = np.zeros((2, 2), np.int32)
     ncol, ndep = ctypes.c_int(), ctypes.c_int64()
     dep = np.zeros(0, np.int32)
-    ok = lib.pie_scan_schedule(pos.ctypes.data, 2, 16, 32, 32, None, ctypes.byref(ncol), None, None, None, None, 0,
+    ok = lib.pie_scan_schedule(pos.ctypes.data, 2, 16, 32, 32, None, 0, ctypes.byref(ncol), None, None, None, None, 0,
                                ctypes.byref(ndep))
     assert ok == 0 and ncol.value == 2 and ndep.value == 1
     # a dep buffer too small for the lists is refused, with the count still reported
-    assert lib.pie_scan_schedule(pos.ctypes.data, 2, 16, 32, 32, None, ctypes.byref(ncol), None, None, None,
+    assert lib.pie_scan_schedule(pos.ctypes.data, 2, 16, 32, 32, None, 0, ctypes.byref(ncol), None, None, None,
                                  dep.ctypes.data, 0, ctypes.byref(ndep)) == -1
     assert ndep.value == 1 and b"needed" in lib.pft_last_error()
-    assert lib.pie_scan_schedule(None, 2, 16, 32, 32, None, ctypes.byref(ncol), None, None, None, None, 0,
+    assert lib.pie_scan_schedule(None, 2, 16, 32, 32, None, 0, ctypes.byref(ncol), None, None, None, None, 0,
                                  ctypes.byref(ndep)) == -1
-    assert lib.pie_scan_schedule(pos.ctypes.data, 2, 40, 32, 32, None, ctypes.byref(ncol), None, None, None, None,
+    assert lib.pie_scan_schedule(pos.ctypes.data, 2, 40, 32, 32, None, 0, ctypes.byref(ncol), None, None, None, None,
                                  0, ctypes.byref(ndep)) == -1                 # patch larger than the object

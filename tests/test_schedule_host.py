@@ -71,6 +71,24 @@ def test_spiral_schedule_in_any_order(pft, seed):
     assert depth.max() <= S["ncolours"]
 
 
+@pytest.mark.parametrize("seed", [None, 5])
+def test_sequential_schedule_is_the_visiting_order(pft, seed):
+    """One colour per position: the schedule is the visiting order itself
+    (Section 2.1's sequential j, or Section 4.2's random order), and the
+    dataflow predecessors are still sound, now for that order."""
+    P = synth.spiral_problem(side=384, n=64, count=300, peak_photons=None, M=16)
+    order = np.arange(300) if seed is None else np.random.default_rng(seed).permutation(300)
+    S = pft.pie_scan_schedule(P["pos"], 64, P["obj"].shape, None if seed is None else order, sequential=True)
+    assert S["ncolours"] == 300
+    assert np.array_equal(S["colour"], opie.sequential_colouring(order))
+    assert np.array_equal(S["sched"], order)
+    check_predecessors(P["pos"], 64, S)
+    # disjoint patches still get no predecessor: four touching patches
+    S = pft.pie_scan_schedule(np.array([[0, 0], [0, 16], [16, 0], [16, 16]], np.int32), 16, (32, 32),
+                              sequential=True)
+    assert S["ncolours"] == 4 and len(S["dep"]) == 0
+
+
 def test_disjoint_and_single_positions(pft):
     # patches that touch but do not overlap: one colour, no predecessors
     pos = np.array([[0, 0], [0, 16], [16, 0], [16, 16]], np.int32)
