@@ -192,8 +192,10 @@ int pft_fft_crop(const void* in, void* out, int n, int M, int64_t batch, void* s
  *                0 <= row <= obj_h - n, 0 <= col <= obj_w - n;
  *   intensities: device float [N][n][n], far-field intensities in FFT order
  *                (not shifted). The context stores d = sqrt(I) and the
- *                centred crop d^crop (the cropped data of Algorithm 3).
- *   Synchronises `stream` once. The caller's buffers may be freed afterwards.
+ *                centred crop d^crop (the cropped data of Algorithm 3);
+ *                negative counts are taken as 0, and a NaN or infinite
+ *                intensity makes the call return PFT_ERR_NONFINITE.
+ *   Synchronises `stream`. The caller's buffers may be freed afterwards.
  */
 typedef struct pie_ctx pie_ctx;
 
@@ -355,6 +357,23 @@ int pie_tv_step(pie_ctx* ctx, void* object, double lambda, double eps, void* str
  * still runs positions whose patches do not overlap at the same time).
  * Synchronises the device. */
 int pie_ctx_set_order(pie_ctx* ctx, const int32_t* order, int one_per_colour);
+
+/* Test hook for the error path of the bounded device waits. kind:
+ * PIE_TEST_WAIT_GRID_BARRIER raises the target of every grid barrier of a
+ * PIE_LAUNCH_PERSISTENT sweep by one, PIE_TEST_WAIT_DATAFLOW the completion
+ * count every PIE_LAUNCH_DATAFLOW position waits for, so that wait can never
+ * be met (no CTA ever adds the missing arrival); PIE_TEST_WAIT_NONE (normal
+ * use) turns it off. The next sweep in that launch form then runs the wait's
+ * 2 s timeout: the waiting CTA sets the sweep's error word, every other CTA
+ * sees it and stops waiting, every cluster barrier is still matched, so the
+ * launch ends with the object unspecified. A sweep called with `stats`
+ * (which synchronises) returns PFT_ERR_TIMEOUT itself; otherwise the next
+ * pie_iteration* or warm_start_then_refine call returns it. The call after
+ * that runs normally. Synchronises the device when the setting changes. */
+#define PIE_TEST_WAIT_NONE         0
+#define PIE_TEST_WAIT_GRID_BARRIER 1
+#define PIE_TEST_WAIT_DATAFLOW     2
+int pie_ctx_test_unreachable_wait(pie_ctx* ctx, int kind);
 
 /* How coloured sweeps of `transform` are launched (PIE_LAUNCH_*):
  * PIE_LAUNCH_PERSISTENT runs the whole sweep as one cooperative launch (the

@@ -27,10 +27,15 @@ constexpr int kWarps = kThreads / 32;
 
 // ------------------------------------------------------------ helper kernels
 __global__ void k_amplitudes(const float* __restrict__ I, float* __restrict__ d, float* __restrict__ dc,
-                             int npos, int n, int M) {
+                             int npos, int n, int M, unsigned* __restrict__ nonfinite) {
   const long long tot = (long long)npos * n * n;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x)
-    d[i] = sqrtf(fmaxf(I[i], 0.f));
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const float v = I[i];
+    bad |= !isfinite(v);  // fmaxf below would turn a NaN count into 0
+    d[i] = sqrtf(fmaxf(v, 0.f));
+  }
+  if (bad) atomicOr(nonfinite, 1u);
   const long long totc = (long long)npos * M * M;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < totc; i += (long long)gridDim.x * blockDim.x) {
     const long long j = i / (M * M);
@@ -252,6 +257,7 @@ struct pie_ctx {
   int* d_coloff = nullptr;     // colour offsets into d_sched [ncol + 1] (persistent sweeps)
   int max_colour = 0;          // positions in the largest colour
   unsigned* d_gbar = nullptr;  // [2]: grid-barrier arrivals, error word
+  int test_wait = PIE_TEST_WAIT_NONE;  // pie_ctx_test_unreachable_wait
   int* h_gstatus = nullptr;    // mapped host status word of the persistent sweeps
   int* d_gstatus = nullptr;
   // launch form of the coloured sweeps per transform (autotuned): PIE_LAUNCH_PER_COLOUR,
@@ -466,6 +472,11 @@ int launch_pie(pie_ctx* c, int transform, int mode, PieArgs a, cudaStream_t st) 
         break;
       }
   }
+  // no size that fits the whole colour at once (or only larger clusters are
+  // built, as for 256 x 256 full-FFT frames): the largest built size, whose
+  // clusters loop over the colour's positions
+  for (int q = 3; q >= 0 && !c->kern[t][mode][ci].fn; --q)
+    if (c->kern[t][mode][q].fn) ci = q;
   const PieKernel& k = c->kern[t][mode][ci];
   if (!k.fn) return pfth::set_error(PFT_ERR_UNSUPPORTED, "no PIE kernel for this transform and mode");
   const long long clusters = std::min<long long>(a.count, std::max<long long>(1, c->cap[t][mode][ci] / k.cluster));
@@ -536,6 +547,8 @@ int launch_pie_persistent(pie_ctx* c, int transform, PieArgs a, cudaStream_t st)
   a.dep_off = flow ? c->d_dep_off : nullptr;
   a.dep = flow ? c->d_dep : nullptr;
   a.done = flow ? c->d_done : nullptr;
+  a.bar_extra = c->test_wait == PIE_TEST_WAIT_GRID_BARRIER ? 1u : 0u;
+  a.dep_extra = c->test_wait == PIE_TEST_WAIT_DATAFLOW ? 1u : 0u;
   PFT_CUDA_TRY(cudaMemsetAsync(c->d_gbar, 0, 2 * sizeof(unsigned), st));
   if (flow) PFT_CUDA_TRY(cudaMemsetAsync(c->d_done, 0, sizeof(unsigned) * c->npos, st));
   PftConst cst = c->plan.cst;
@@ -796,11 +809,21 @@ int pie_ctx_create(pie_ctx** out, const pie_problem* pb, const void* probe, cons
   }
   PIE_CUDA(cudaMalloc(&c->d_pos, sizeof(int2) * N));
   PIE_CUDA(cudaMemcpyAsync(c->d_pos, c->h_pos.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, st));
-  // amplitudes
+  // amplitudes (d_red[7] counts non-finite intensities)
+  PIE_CUDA(cudaMalloc(&c->d_red, sizeof(double) * 8));
+  PIE_CUDA(cudaMallocHost(&c->h_red, sizeof(double) * 8));
+  PIE_CUDA(cudaMemsetAsync(c->d_red, 0, sizeof(double) * 8, st));
   PIE_CUDA(cudaMalloc(&c->d_amp, sizeof(float) * (size_t)N * n * n));
   PIE_CUDA(cudaMalloc(&c->d_ampc, sizeof(float) * (size_t)N * M * M));
-  k_amplitudes<<<grid_for((long long)N * n * n), kThreads, 0, st>>>(intensities, c->d_amp, c->d_ampc, N, n, M);
+  k_amplitudes<<<grid_for((long long)N * n * n), kThreads, 0, st>>>(intensities, c->d_amp, c->d_ampc, N, n, M,
+                                                                   reinterpret_cast<unsigned*>(c->d_red + 7));
   PIE_CUDA(cudaGetLastError());
+  PIE_CUDA(cudaMemcpyAsync(c->h_red + 7, c->d_red + 7, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PIE_CUDA(cudaStreamSynchronize(st));
+  if (*reinterpret_cast<const unsigned*>(c->h_red + 7) != 0u) {
+    pie_ctx_destroy(c);
+    return pfth::set_error(PFT_ERR_NONFINITE, "the intensities hold a NaN or infinite value");
+  }
   // colouring
   colour_positions(c);
   PIE_CUDA(cudaMalloc(&c->d_sched, sizeof(int) * N));
@@ -810,8 +833,6 @@ int pie_ctx_create(pie_ctx** out, const pie_problem* pb, const void* probe, cons
   PIE_CUDA(cudaMalloc(&c->d_inv_illum, sizeof(float) * HW));
   PIE_CUDA(cudaMalloc(&c->d_mask, HW));
   PIE_CUDA(cudaMalloc(&c->d_prev, sizeof(float2) * HW));
-  PIE_CUDA(cudaMalloc(&c->d_red, sizeof(double) * 8));
-  PIE_CUDA(cudaMallocHost(&c->h_red, sizeof(double) * 8));
   PIE_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   if (pb->mode == PIE_MODE_BATCHED) PIE_CUDA(cudaMalloc(&c->d_acc, sizeof(float2) * HW));
   PIE_CUDA(cudaMemsetAsync(c->d_inv_illum, 0, sizeof(float) * HW, st));
@@ -1028,7 +1049,8 @@ int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, 
   if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
     return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
   if (transform == PIE_TRANSFORM_FULL && !c->have_full)
-    return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n in {16, 32, 64, 128}, not %d", c->n);
+    return pfth::set_error(PFT_ERR_UNSUPPORTED, "full-FFT PIE is built for n in {16, 32, 64, 128, 256}, not %d",
+                           c->n);
   if (c->h_gstatus && *c->h_gstatus != PFT_OK) {
     const int e = *c->h_gstatus;
     *c->h_gstatus = PFT_OK;
@@ -1050,10 +1072,16 @@ int iterate(pie_ctx* c, void* object, int transform, double beta, double gamma, 
   PFT_CUDA_TRY(cudaGraphLaunch(exec, st));
   if (stats) {
     PFT_CUDA_TRY(cudaStreamSynchronize(st));
+    if (c->h_gstatus && *c->h_gstatus != PFT_OK) {  // this sweep's own device-side failure
+      const int e = *c->h_gstatus;
+      *c->h_gstatus = PFT_OK;
+      return pfth::set_error(e, e == PFT_ERR_TIMEOUT ? "a bounded wait of this sweep timed out"
+                                                     : "this sweep's kernel ran without its cluster shape");
+    }
     const double n2 = (double)c->n * (double)c->n;
     stats->phi = c->h_red[0] / ((double)c->npos * n2);
     stats->rel_change = c->h_red[2] > 0 ? std::sqrt(c->h_red[1] / c->h_red[2]) : 0.0;
-    if (!std::isfinite(stats->phi) || !std::isfinite(stats->rel_change))
+    if (!std::isfinite(stats->phi) || !std::isfinite(c->h_red[1]) || !std::isfinite(c->h_red[2]))
       return pfth::set_error(PFT_ERR_NONFINITE, "non-finite objective or object change");
   }
   return PFT_OK;
@@ -1138,6 +1166,19 @@ int pie_ctx_set_persistent(pie_ctx* c, int transform, int persistent) {
   return PFT_OK;
 }
 
+int pie_ctx_test_unreachable_wait(pie_ctx* c, int kind) {
+  if (!c) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (kind < PIE_TEST_WAIT_NONE || kind > PIE_TEST_WAIT_DATAFLOW)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown wait kind %d", kind);
+  if (c->test_wait != kind) {
+    PFT_CUDA_TRY(cudaDeviceSynchronize());
+    c->test_wait = kind;
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);  // the hook is baked into captured sweeps
+    c->graphs.clear();
+  }
+  return PFT_OK;
+}
+
 int pie_ctx_set_order(pie_ctx* c, const int32_t* order, int one_per_colour) {
   if (!c) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
   std::vector<int> ord;
@@ -1168,6 +1209,8 @@ int pie_nrmse(pie_ctx* c, const void* object, const void* truth, double* out, vo
   PFT_CUDA_TRY(cudaGetLastError());
   PFT_CUDA_TRY(cudaMemcpyAsync(c->h_red + 3, c->d_red + 3, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
   PFT_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int q = 3; q < 7; ++q)  // std::max below would turn a NaN sum into 0
+    if (!std::isfinite(c->h_red[q])) return pfth::set_error(PFT_ERR_NONFINITE, "non-finite object or truth");
   const double ip = std::hypot(c->h_red[3], c->h_red[4]);
   const double e2 = std::max(0.0, c->h_red[5] + c->h_red[6] - 2.0 * ip);
   *out = c->h_red[6] > 0 ? std::sqrt(e2 / c->h_red[6]) : 0.0;

@@ -17,7 +17,7 @@ struct Entry {
 
 template <int N, int MODE, int C, bool CLAIM = false>
 void add(std::vector<Entry>& v) {
-  if constexpr (PieFullShape<N, C>::VALID) {
+  if constexpr (PieFullShape<N, C>::VALID && PieFullShape<N, C>::FITS) {
     PieKernel k;
     k.fn = (const void*)k_pie_full<N, MODE, C, kThreads, CLAIM>;
     k.smem = PieFullShape<N, C>::SMEM;
@@ -40,12 +40,21 @@ void add_size(std::vector<Entry>& v) {
   add<N, MODE_BATCHED, 4>(v);
 }
 
+// 256 x 256 frames: the spectrum fits shared memory only when each of 8 CTAs
+// holds an eighth of it (about 167 KB per CTA), so only clusters of 8 exist.
+void add_size_256(std::vector<Entry>& v) {
+  add<256, MODE_COLOURED, 8>(v);
+  add<256, MODE_COLOURED, 8, true>(v);
+  add<256, MODE_BATCHED, 8>(v);
+}
+
 std::vector<Entry> build_table() {
   std::vector<Entry> v;
   add_size<16>(v);
   add_size<32>(v);
   add_size<64>(v);
   add_size<128>(v);
+  add_size_256(v);
   return v;
 }
 

@@ -88,6 +88,11 @@ struct PieArgs {
   // by running clusters, so every wait ends without the clusters being
   // co-resident (used when several sweeps share the GPU).
   unsigned* ticket;
+  // test hook (pie_ctx_test_unreachable_wait): added to the target of every
+  // grid barrier (bar_extra) or dataflow wait (dep_extra); zero in normal use.
+  // A non-zero value makes that wait unreachable, so its bounded timeout runs.
+  unsigned bar_extra;
+  unsigned dep_extra;
 };
 
 template <int C>
@@ -182,7 +187,7 @@ __device__ __forceinline__ void wait_deps(const PieArgs& a, int s) {
       while (true) {
         unsigned v;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
-        if (v >= (unsigned)C) break;
+        if (v >= (unsigned)C + a.dep_extra) break;
         if (*reinterpret_cast<volatile int*>(a.gerr)) {
           ok = false;
           break;
@@ -223,10 +228,12 @@ using ResAcc = typename std::conditional<MODE == MODE_GRAD, double, float>::type
 
 template <int MODE>
 __device__ __forceinline__ float2 residual(float2 Psi, float d, ResAcc<MODE>& acc) {
+  // m2 != 0 rather than m2 > 0: the same for every finite m2 >= 0, but a NaN
+  // coefficient takes the general branch and stays NaN (reported by the host)
   const float m2 = cabs2(Psi);
   if (MODE == MODE_GRAD) {
     // sgn(0) = 0; the gradient of sum (|Psi| - d)^2 is 2 R
-    if (m2 > 0.f) {
+    if (m2 != 0.f) {
       const float m = sqrtf(m2);
       const float diff = m - d;
       acc += (double)diff * (double)diff;
@@ -237,7 +244,7 @@ __device__ __forceinline__ float2 residual(float2 Psi, float d, ResAcc<MODE>& ac
   }
   // theta(0) = 0: a zero coefficient is replaced by d
   float2 R;
-  if (m2 > 0.f) {
+  if (m2 != 0.f) {
     R = cscale(Psi, 1.f - d * rsqrtf(m2));
   } else {
     R = make_float2(-d, 0.f);
@@ -466,7 +473,10 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
   const int rounds = (MODE == MODE_COLOURED && a.pacc) ? 2 : 1;
   for (int col = 0; col < ncol; ++col) {
   if (col > 0) {
-    if (!grid_barrier(a.gbar, (unsigned)col * gridDim.x, a.gerr, a.gstatus)) break;
+    if (!grid_barrier(a.gbar, (unsigned)col * gridDim.x + a.bar_extra, a.gerr, a.gstatus)) {
+      cp_async_wait_all();  // the next colour's prefetch lands before the CTA leaves
+      break;
+    }
     if (it < ce) gather_obj(resolve<M * M>(a, it));
   }
   while (it < ce) {
@@ -602,6 +612,7 @@ struct PieFullShape {
   static constexpr int OFF_RED = (C == 1) ? OFF_C + N * SCS : OFF_R + RN * SRS;
   static constexpr int OFF_D = OFF_RED + 16;  // amplitudes of the CTA's slot columns: [N][CN] floats
   static constexpr size_t SMEM = sizeof(float2) * (OFF_D + (N * CN + 1) / 2);
+  static constexpr bool FITS = SMEM <= 232448;  // 227 KB of shared memory per CTA
 };
 
 template <int N, int MODE, int C, int NT, bool CLAIM = false>
@@ -672,7 +683,10 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
   const int rounds = (MODE == MODE_COLOURED && a.pacc) ? 2 : 1;
   for (int col = 0; col < ncol; ++col) {
   if (col > 0) {
-    if (!grid_barrier(a.gbar, (unsigned)col * gridDim.x, a.gerr, a.gstatus)) break;
+    if (!grid_barrier(a.gbar, (unsigned)col * gridDim.x + a.bar_extra, a.gerr, a.gstatus)) {
+      cp_async_wait_all();  // the next colour's prefetch lands before the CTA leaves
+      break;
+    }
     if (it < ce) gather_obj(resolve<N * N>(a, it));
   }
   while (it < ce) {

@@ -26,6 +26,7 @@ TRANSFORM_PFT, TRANSFORM_FULL = 0, 1
 MODE_COLOURED, MODE_BATCHED = 0, 1
 LAUNCH_PER_COLOUR, LAUNCH_PERSISTENT, LAUNCH_DATAFLOW = 0, 1, 2
 PROBE_STEP_NORMALISED, PROBE_STEP_SCALAR = 0, 1
+TEST_WAIT_NONE, TEST_WAIT_GRID_BARRIER, TEST_WAIT_DATAFLOW = 0, 1, 2
 _ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "OOM"}
 
 
@@ -118,6 +119,7 @@ def load() -> ctypes.CDLL:
         "pie_tv_step": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_double, _P]),
         "pie_ctx_set_order": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "pie_ctx_set_persistent": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+        "pie_ctx_test_unreachable_wait": (ctypes.c_int, [_P, ctypes.c_int]),
         "pie_amp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
         "pie_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
@@ -388,6 +390,12 @@ class PieContext:
         per-position waits on overlapping predecessors)."""
         form = int(persistent) if not isinstance(persistent, bool) else (1 if persistent else 0)
         _check(load().pie_ctx_set_persistent(self._h, transform, form))
+
+    def test_unreachable_wait(self, kind: int):
+        """Test hook: TEST_WAIT_GRID_BARRIER / TEST_WAIT_DATAFLOW make every
+        wait of that launch form unreachable, so the next such sweep runs its
+        bounded timeout and reports PFT_ERR_TIMEOUT; TEST_WAIT_NONE turns it off."""
+        _check(load().pie_ctx_test_unreachable_wait(self._h, int(kind)))
 
     def iteration_blind(self, obj, transform: int = TRANSFORM_FULL, beta: float = 1.0, gamma: float = 1.0,
                         stats: bool = True, stream=None, probe_step: int = 0):

@@ -134,3 +134,36 @@ def test_batch_equals_separate_contexts_at_full_recipe(env):
         ctx.iteration(z, pft.TRANSFORM_PFT, 1.0, stats=False)
         torch.cuda.synchronize()
         assert torch.equal(z, objs[i]), i
+
+
+@pytest.mark.parametrize("transform", ["pft", "full"])
+def test_recipe_classes_match_oracle(env, transform):
+    """One instance of every shape class (n, M) of the 64-instance recipe, the
+    one with the fewest positions, swept together in one batch; each object is
+    compared with the oracle's sweep of that instance (noise-free data, a start
+    within +-10 % of the truth, so the comparison is well conditioned). The
+    full transform includes the 256^2 probes' 8-CTA kernel."""
+    torch, pft = env
+    specs = synth.uneven_batch_recipe(64)
+    pick = {}
+    for sp in specs:
+        key = (sp["n"], sp["M"])
+        if key not in pick or sp["npos"] < pick[key]["npos"]:
+            pick[key] = sp
+    assert len(pick) >= 8
+    insts = []
+    for key in sorted(pick):
+        inst = synth.make_instance(pick[key])
+        inst["intensities"] = synth.simulate_intensities(inst["obj"], inst["probe"], inst["pos"])
+        rng = np.random.default_rng(pick[key]["seed"])
+        inst["init"] = inst["obj"] * (1 + 0.2 * (rng.random(inst["obj"].shape) - 0.5))
+        insts.append(inst)
+    B = pft.PieBatch(to_gpu(insts, torch))
+    assert B.classes()[0] == len(insts)
+    objs = [torch.from_numpy(i["init"].astype(np.complex64)).cuda() for i in insts]
+    tr = pft.TRANSFORM_PFT if transform == "pft" else pft.TRANSFORM_FULL
+    phi = B.iteration(objs, tr, 1.0)
+    for i, inst in enumerate(insts):
+        zo, po = oracle_sweep(inst, transform, "coloured", 1.0)
+        assert rel(objs[i].cpu().numpy(), zo) < TOL, (i, inst["probe"].shape, inst["M"])
+        assert phi[i] == pytest.approx(po, rel=1e-4)
