@@ -8,9 +8,9 @@ struct pft_plan {
   double xi1, xi2, eps;
   int path, precision;
   pftk::PftConst cst;     // B rows for both axes (kernel parameter space)
-  float2* d_W = nullptr;  // [2][RMAX][M] : W'[axis][j][t_idx] (FP32 from FP64)
-  float2* d_twp = nullptr;  // [16] : e^{-2 pi i m / p}, m < p/2
-  float* d_B = nullptr;     // [2][q][RMAX] full B table (inspection only)
+  float2* d_W = nullptr;  // W' of axis 1 ([RMAX][M1]) then axis 2 ([RMAX][M2]), j-major (FP32 from FP64)
+  float2* d_twp = nullptr;  // [2][32] : e^{-2 pi i m / p_axis}, m < p_axis / 2 (axis 2 at +32)
+  float* d_B = nullptr;     // B of axis 1 ([q1][RMAX]) then axis 2 ([q2][RMAX]) (inspection only)
   int kid = -1;             // index in the frame-kernel registry
   void* d_tc = nullptr;     // split-BF16 tensor-core table (MMA operand layout)
   void* d_tc_adj = nullptr; // its adjoint table conj(A)^T
@@ -23,19 +23,21 @@ struct pft_plan {
 
 namespace pfth {
 
-// Frame kernels built for one (P, Q, M/P) shape.
+// Frame kernels built for one pair of 1-D shapes: (P1, Q1, M1/P1) along axis 1
+// (columns, length n1) and (P2, Q2, M2/P2) along axis 2 (rows, length n2).
 struct FrameKernels {
-  int P, Q, MP;
+  int P1, Q1, MP1, P2, Q2, MP2;
   const void* fwd;
   const void* adj;
   size_t smem;
 };
 int frame_kernel_count();
 const FrameKernels* frame_kernels(int id);
-int find_frame_kernels(int P, int Q, int MP);
+int find_frame_kernels(int P1, int Q1, int MP1, int P2, int Q2, int MP2);
 
 // Builds a square plan's tables; used by pft_plan_create and the PIE context.
 int build_plan(pft_plan* p, int n, int M, int P, double eps, int r_force);
+int build_plan2(pft_plan* p, int n1, int n2, int M1, int M2, int P1, int P2, double eps, int r1, int r2);
 
 // Split-BF16 tensor-core path (pft_tc.cu).
 bool tc_supported(int n, int M, int p);

@@ -184,21 +184,30 @@ def choose_r(eps: float, ratio: float) -> int:
 
 # ------------------------------------------------------------------- plans
 class Plan:
-    """A square PFT plan (Algorithm 4): n x n frames -> centred M x M outputs."""
+    """A PFT plan (Algorithm 4): n1 x n2 frames -> centred M1 x M2 outputs.
+
+    Plan(n, M) is square; n2, M2, p2 (default: as axis 1) make it rectangular
+    (PREC_FP32; each axis has its own p, q, r and tables)."""
 
     def __init__(self, n: int, M: int, p: int = 0, eps: float = 1e-7, r: int = 0,
-                 path: int = PATH_AUTO, precision: int = PREC_FP32):
+                 path: int = PATH_AUTO, precision: int = PREC_FP32, n2: int | None = None,
+                 M2: int | None = None, p2: int | None = None):
         lib = load()
         h = ctypes.c_void_p()
-        _check(lib.pft_plan_create(ctypes.byref(h), n, n, M, M, p, p, eps, r, r, path, precision))
+        n2 = n if n2 is None else n2
+        M2 = M if M2 is None else M2
+        p2 = p if p2 is None else p2
+        _check(lib.pft_plan_create(ctypes.byref(h), n, n2, M, M2, p, p2, eps, r, r, path, precision))
         self._h = h
         info = PlanInfo()
         _check(lib.pft_plan_info_get(h, ctypes.byref(info)))
         self.info = {f: getattr(info, f) for f, _ in PlanInfo._fields_}
         self.n, self.M = n, M
+        self.n2, self.M2 = n2, M2
 
     def tables(self, axis: int = 0) -> tuple[np.ndarray, np.ndarray]:
-        q, r, M = self.info["q1"], self.info["r1"], self.M
+        ax = "2" if axis else "1"
+        q, r, M = self.info["q" + ax], self.info["r" + ax], self.M2 if axis else self.M
         B = np.zeros((q, r), dtype=np.float32)
         W = np.zeros((M, r), dtype=np.complex64)
         _check(load().pft_plan_tables(self._h, axis, B.ctypes.data, W.ctypes.data))
@@ -206,20 +215,20 @@ class Plan:
 
     def forward(self, x, out=None, stream=None):
         import torch
-        _need(x, torch.complex64, (self.n, self.n), "x")
+        _need(x, torch.complex64, (self.n, self.n2), "x")
         lead = x.shape[:-2]
         if out is None:
-            out = torch.empty(*lead, self.M, self.M, dtype=torch.complex64, device=x.device)
+            out = torch.empty(*lead, self.M, self.M2, dtype=torch.complex64, device=x.device)
         batch = int(np.prod(lead)) if len(lead) else 1
         _check(load().pft_forward(self._h, _ptr(x), _ptr(out), batch, _stream(stream)))
         return out
 
     def adjoint(self, y, out=None, stream=None):
         import torch
-        _need(y, torch.complex64, (self.M, self.M), "y")
+        _need(y, torch.complex64, (self.M, self.M2), "y")
         lead = y.shape[:-2]
         if out is None:
-            out = torch.empty(*lead, self.n, self.n, dtype=torch.complex64, device=y.device)
+            out = torch.empty(*lead, self.n, self.n2, dtype=torch.complex64, device=y.device)
         batch = int(np.prod(lead)) if len(lead) else 1
         _check(load().pft_adjoint(self._h, _ptr(y), _ptr(out), batch, _stream(stream)))
         return out

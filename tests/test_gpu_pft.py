@@ -151,3 +151,47 @@ def test_edge_cases_and_errors(env):
     assert e.value.code == -2
     with pytest.raises(pft.PftError):
         pft.Plan(64, 32, eps=1e-12)  # needs more than 13 terms
+
+
+# rectangular frames: (n1, n2, M1, M2); p = M / 2 per axis
+RECT = [(128, 256, 32, 32), (256, 128, 32, 32), (64, 128, 32, 32), (128, 128, 32, 64), (256, 256, 64, 32),
+        (128, 128, 16, 32)]
+
+
+@pytest.mark.parametrize("n1,n2,M1,M2", RECT)
+def test_rectangular_plans_match_oracle(env, n1, n2, M1, M2):
+    """Rectangular frames and outputs (Algorithm 4 per axis, each axis with its
+    own p, q, r and tables): forward and adjoint against the oracle's
+    Algorithm 5 on 6 frames, and the adjoint identity."""
+    torch, pft = env
+    plan = pft.Plan(n1, M1, n2=n2, M2=M2)
+    i = plan.info
+    assert (i["n1"], i["n2"], i["M1"], i["M2"]) == (n1, n2, M1, M2)
+    assert (i["p1"], i["p2"]) == (M1 // 2, M2 // 2) and (i["q1"], i["q2"]) == (2 * n1 // M1, 2 * n2 // M2)
+    P1, P2 = coeffs.plan_2d(n1, n2, M1, M2, M1 // 2, M2 // 2)
+    rng = np.random.default_rng(n1 + 3 * n2 + 5 * M1 + 7 * M2)
+    x = (rng.standard_normal((6, n1, n2)) + 1j * rng.standard_normal((6, n1, n2))).astype(np.complex64)
+    y = (rng.standard_normal((6, M1, M2)) + 1j * rng.standard_normal((6, M1, M2))).astype(np.complex64)
+    Ax = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert Ax.shape == (6, M1, M2)
+    assert rel_frames(Ax, opft.pft2(x.astype(np.complex128), P1, P2)).max() < TOL
+    Ahy = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert Ahy.shape == (6, n1, n2)
+    assert rel_frames(Ahy, opft.pft2_adjoint(y.astype(np.complex128), P1, P2)).max() < TOL
+    lhs = np.vdot(y.astype(np.complex128), Ax.astype(np.complex128))
+    rhs = np.vdot(Ahy.astype(np.complex128), x.astype(np.complex128))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    # each axis has its own tables: axis 2's are those of a square plan of that axis's shape
+    B2, W2 = plan.tables(1)
+    B2s, W2s = pft.Plan(n2, M2).tables(0)
+    assert W2.shape == (M2, 13) and np.array_equal(W2, W2s) and np.array_equal(B2, B2s)
+
+
+def test_rectangular_plan_limits(env):
+    torch, pft = env
+    with pytest.raises(pft.PftError) as e:   # rectangular plans are FP32
+        pft.Plan(128, 32, n2=256, precision=pft.PREC_SPLIT_BF16)
+    assert e.value.code == -2
+    with pytest.raises(pft.PftError) as e:   # a shape pair with no kernel built
+        pft.Plan(32, 16, n2=256, M2=64)
+    assert e.value.code == -2
