@@ -175,6 +175,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
 // 2 s. A wait that gives up (or finds that another CTA gave up) sets the error
 // words and returns without waiting: the CTA still runs every item and cluster
 // barrier of its list, so the launch ends, and the host reports the timeout.
+// No fence follows the polls: each lane's acquire load synchronises with its
+// predecessor's release (signal_done), the CTA barrier below orders that before
+// every thread's later patch reads, and those read L2 (ld.global.cg), not L1.
 template <int C>
 __device__ __forceinline__ void wait_deps(const PieArgs& a, int s) {
   if (threadIdx.x < 32) {
@@ -204,19 +207,18 @@ __device__ __forceinline__ void wait_deps(const PieArgs& a, int s) {
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
 
-// Dataflow sweep: this CTA's part of item s's update is written (every thread's
-// stores ordered before the release by the barrier and the fence).
+// Dataflow sweep: this CTA's part of item s's update is written. The CTA
+// barrier orders every thread's stores before thread 0's release-add, and a
+// release is cumulative, so a successor whose acquire load sees the count sees
+// the whole update (one release-add costs less than a fence and a relaxed add).
 __device__ __forceinline__ void signal_done(const PieArgs& a, int s) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(a.done + s, 1u);
-  }
+  if (threadIdx.x == 0)
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(a.done + s), "r"(1u) : "memory");
 }
 
 // Modulus-projection residual (Eq. 3) and its contribution to the objective.
