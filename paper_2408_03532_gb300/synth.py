@@ -152,14 +152,17 @@ def random_frames(batch: int, n1: int, n2: int | None = None,
 # Workload recipes (sizes of the paper-shaped configurations)
 # ---------------------------------------------------------------------------
 
-def small_raster_problem(noise: bool = False) -> dict:
-    """128^2 object, 32^2 probe, 8 x 8 raster of stride 12 (offset 6), M = 16."""
-    obj = make_object(128)
+def small_raster_problem(noise: bool = False, seed_shift: int = 0) -> dict:
+    """128^2 object, 32^2 probe, 8 x 8 raster of stride 12 (offset 6), M = 16.
+
+    ``seed_shift`` draws another instance (object, noise and start move; the
+    probe and the raster stay)."""
+    obj = make_object(128, seed=SEED_OBJECT + seed_shift)
     probe = make_probe(32)
     pos = raster_scan(8, 8, 12, 6)
-    inten = simulate_intensities(obj, probe, pos, 1e4 if noise else None)
+    inten = simulate_intensities(obj, probe, pos, 1e4 if noise else None, seed=SEED_POISSON + seed_shift)
     return dict(obj=obj, probe=probe, pos=pos, intensities=inten, M=16,
-                init=random_init(128))
+                init=random_init(128, seed=SEED_INIT + seed_shift))
 
 
 def spiral_problem(side: int = 1024, n: int = 128, count: int = 3600,
