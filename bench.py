@@ -631,14 +631,14 @@ def _csrc_sha(name: str) -> str:
 # writes are the L2's write-back of object lines. Valid only for the sources
 # hashed below (None otherwise).
 PIE_TRAFFIC = {
-    "pie_pft": {"sources": {"pie_kernels.cuh": "6e58ca8ce5e3031713c77d08f96f5a83fb7f676e91e54a1fc30f7430db3772a6",
+    "pie_pft": {"sources": {"pie_kernels.cuh": "4c1d9a69170bdf40f5560292d9d84d2d0bfaaa72ff0277da60460241cc03699c",
                             "pft_core.cuh": "4dfa31346e0ac684953fa89ce8271d10337e260a8ecc858bb0f8b85d03925495",
                             "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
-                "read_per_position": 4608 / 128, "write_per_position": 1150208 / 128},
-    "pie_full": {"sources": {"pie_kernels.cuh": "6e58ca8ce5e3031713c77d08f96f5a83fb7f676e91e54a1fc30f7430db3772a6",
+                "read_per_position": 3328 / 128, "write_per_position": 1179904 / 128},
+    "pie_full": {"sources": {"pie_kernels.cuh": "4c1d9a69170bdf40f5560292d9d84d2d0bfaaa72ff0277da60460241cc03699c",
                              "fft_core.cuh": "dd2552f57edd2220bfec6952833eeb81f9edcb4dd2d2b1e7f4bd407c1bbe064a",
                              "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
-                 "read_per_position": 8484608 / 128, "write_per_position": 24832 / 128},
+                 "read_per_position": 8490496 / 128, "write_per_position": 25600 / 128},
 }
 
 
@@ -857,11 +857,19 @@ def measure_batch64(pft, synth, torch, dev, stream, flush, reps: int = 3) -> dic
             row[f"{tname}_frames_per_s"] = pos / (ms / 1e3)
             row[f"{tname}_alu_frac"] = fpos * pos / (ms / 1e3) / 1e12 / peak
         row["launches_per_sweep"] = B.classes()[1]
+        # the same class alone in the dataflow form (one launch per sweep): set against the per-colour
+        # time, this separates the form's own cost from the cost of classes sharing the GPU
+        B.set_launch(pft.LAUNCH_DATAFLOW)
+        objs = [inits[i].clone() for i in idx]
+        row["pft_dataflow_sweep_ms"] = sweep_ms(B, objs, pft.TRANSFORM_PFT)
         B.close()
         per.append(row)
     out["per_class"] = per
-    out["per_class_note"] = ("each class swept alone in the per-colour launch form; alu_frac = the method's FP32 "
-                             "work per position x positions / time / derived FP32 peak (latency-bound kernels)")
+    out["per_class_note"] = ("each class swept alone in the per-colour launch form (and, for the PFT sweep, in the "
+                             "dataflow form); alu_frac = the method's FP32 work per position x positions / time / "
+                             "derived FP32 peak (latency-bound kernels)")
+    out["sum_of_classes_ms"] = {"pft_per_colour": sum(r["pft_sweep_ms"] for r in per),
+                                "pft_dataflow": sum(r["pft_dataflow_sweep_ms"] for r in per)}
     del insts
     torch.cuda.empty_cache()
     return out

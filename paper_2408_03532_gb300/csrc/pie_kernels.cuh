@@ -112,6 +112,59 @@ struct Cluster {
   }
 };
 
+// Asynchronous exchange between the CTAs of a cluster: st.async writes a
+// value into a peer's shared memory and completes `bytes` on the peer's
+// mbarrier; the receiver, which announced the bytes it expects, waits on its
+// own mbarrier (acquire at cluster scope) instead of a cluster-wide barrier.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async2(uint32_t raddr, float2 v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+               ::"r"(raddr), "f"(v.x), "f"(v.y), "r"(rbar) : "memory");
+}
+__device__ __forceinline__ void xbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void xbar_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase of parity `par` (2 s); a timeout sets the error
+// words, and so does finding another CTA's timeout; either way the caller goes on.
+__device__ __forceinline__ void xbar_wait(uint32_t bar, uint32_t par, const PieArgs& a, bool& abort) {
+  if (abort) return;  // an earlier wait of this thread gave up: the sweep is already failed
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+               "selp.b32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(bar), "r"(par) : "memory");
+  if (ok) return;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (true) {
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.b32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(bar), "r"(par) : "memory");
+    if (ok) return;
+    if (a.gerr && *reinterpret_cast<volatile int*>(a.gerr)) {
+      abort = true;
+      return;
+    }
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 2000000000ull) {
+      abort = true;
+      if (a.gerr) atomicExch(a.gerr, 1);
+      if (a.gstatus) {
+        *reinterpret_cast<volatile int*>(a.gstatus) = PFT_ERR_TIMEOUT;
+        __threadfence_system();
+      }
+      return;
+    }
+  }
+}
+
 // A cluster kernel launched without its cluster shape must not address peer
 // shared memory: it records an error and does nothing.
 template <int C>
@@ -455,6 +508,19 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
   for (int i = threadIdx.x; i < 2 * RMAX * M; i += NT) cp_async8(sm + i, gW + i);
   fill_stage_table_async<P>(stw, gtw, P);
   cp_async_commit();
+  // exchange barriers: rows -> column owners (Y) and adjoint columns -> row owners (G)
+  constexpr bool XCH = (C > 1) && !CLAIM;
+  __shared__ __align__(8) unsigned long long s_xbar[2];
+  const uint32_t barY = smem_addr(&s_xbar[0]), barG = smem_addr(&s_xbar[1]);
+  uint32_t parY = 0, parG = 0;
+  bool xabort = false;
+  if constexpr (XCH) {
+    if (threadIdx.x == 0) {
+      xbar_init(barY);
+      xbar_init(barG);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   if (dyn) {
     if (rank == 0 && threadIdx.x == 0) s_claim = (int)atomicAdd(a.ticket, 1u);
     CL::sync();
@@ -504,13 +570,27 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
         else
           xv[l] = cmul(__ldg(p.probe + u * N + v), __ldcg(p.objr + obase + (long long)u * p.obj_w + v));
       }
-      T::forward(xv, k, c.bh[1], sW2, net, [&](int t, float2 val) {
-        float2* dst = CL::map(sY, (unsigned)(t / CM));
-        dst[(t % CM) * S::SYT + u + u / Q] = val;
-      });
+      if constexpr (XCH) {
+        const uint32_t ly = smem_addr(sY);
+        T::forward(xv, k, c.bh[1], sW2, net, [&](int t, float2 val) {
+          const uint32_t r = (uint32_t)(t / CM);
+          st_async2(map_rank(ly + 8u * (uint32_t)((t % CM) * S::SYT + u + u / Q), r), val, map_rank(barY, r));
+        });
+      } else {
+        T::forward(xv, k, c.bh[1], sW2, net, [&](int t, float2 val) {
+          float2* dst = CL::map(sY, (unsigned)(t / CM));
+          dst[(t % CM) * S::SYT + u + u / Q] = val;
+        });
+      }
     }
     if (dyn && round == 0 && rank == 0 && threadIdx.x == 0) s_claim = (int)tk;
-    CL::sync();
+    if constexpr (XCH) {
+      if (threadIdx.x == 0) xbar_expect(barY, (uint32_t)(8 * N * CM));  // every row of this CTA's columns
+      xbar_wait(barY, parY, a, xabort);
+      parY ^= 1u;
+    } else {
+      CL::sync();
+    }
     if (dyn && round == 0) claimed = *CL::map(&s_claim, 0u);
     // 3a. columns (axis 1) of this CTA's slice
     for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
@@ -536,12 +616,25 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
       float2 xv[Q];
       T::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, c.bh[0], sW1, net, xv);
       const int u0 = Q * k;
-      float2* dst = CL::map(sG, (unsigned)(u0 / RN));
       const int tg = rank * CM + tl;
+      if constexpr (XCH) {
+        const uint32_t r = (uint32_t)(u0 / RN);
+        const uint32_t base = map_rank(smem_addr(sG), r), rb = map_rank(barG, r);
 #pragma unroll
-      for (int l = 0; l < Q; ++l) dst[(u0 % RN + l) * S::SG + tg] = xv[l];
+        for (int l = 0; l < Q; ++l) st_async2(base + 8u * (uint32_t)((u0 % RN + l) * S::SG + tg), xv[l], rb);
+      } else {
+        float2* dst = CL::map(sG, (unsigned)(u0 / RN));
+#pragma unroll
+        for (int l = 0; l < Q; ++l) dst[(u0 % RN + l) * S::SG + tg] = xv[l];
+      }
     }
-    CL::sync();
+    if constexpr (XCH) {
+      if (threadIdx.x == 0) xbar_expect(barG, (uint32_t)(8 * RN * M));  // every column of this CTA's rows
+      xbar_wait(barG, parG, a, xabort);
+      parG ^= 1u;
+    } else {
+      CL::sync();
+    }
     if (round == 0) flush_partials<NW>(sred, p.red);
     // 5. adjoint rows and the object update
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
@@ -665,6 +758,19 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
   int it = (persistent ? a.col_off[0] : 0) + (int)(blockIdx.x / C);
   F::fill_async(tw, gtw);
   cp_async_commit();
+  // exchange barriers: rows -> slot-column owners (C) and adjoint columns -> row owners (R)
+  constexpr bool XCH = (C > 1) && !CLAIM;
+  __shared__ __align__(8) unsigned long long s_xbar[2];
+  const uint32_t barC = smem_addr(&s_xbar[0]), barR = smem_addr(&s_xbar[1]);
+  uint32_t parC = 0, parR = 0;
+  bool xabort = false;
+  if constexpr (XCH) {
+    if (threadIdx.x == 0) {
+      xbar_init(barC);
+      xbar_init(barR);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   if (dyn) {
     if (rank == 0 && threadIdx.x == 0) s_claim = (int)atomicAdd(a.ticket, 1u);
     CL::sync();
@@ -715,14 +821,30 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
           x[e] = cmul(__ldg(p.probe + u * N + v), __ldcg(p.objr + obase + (long long)u * p.obj_w + v));
       }
       F::fwd(x, l, tw, net);
+      if constexpr (XCH) {
+        const uint32_t lc = smem_addr(sC);
 #pragma unroll
-      for (int p = 0; p < E; ++p) {
-        const int s = p * L + l;
-        CL::map(sC, (unsigned)(s / CN))[u * S::SCS + s % CN] = x[p];
+        for (int p = 0; p < E; ++p) {
+          const int s = p * L + l;
+          const uint32_t r = (uint32_t)(s / CN);
+          st_async2(map_rank(lc + 8u * (uint32_t)(u * S::SCS + s % CN), r), x[p], map_rank(barC, r));
+        }
+      } else {
+#pragma unroll
+        for (int p = 0; p < E; ++p) {
+          const int s = p * L + l;
+          CL::map(sC, (unsigned)(s / CN))[u * S::SCS + s % CN] = x[p];
+        }
       }
     }
     if (dyn && round == 0 && rank == 0 && threadIdx.x == 0) s_claim = (int)tk;
-    CL::sync();
+    if constexpr (XCH) {
+      if (threadIdx.x == 0) xbar_expect(barC, (uint32_t)(8 * N * CN));  // every row of this CTA's slot columns
+      xbar_wait(barC, parC, a, xabort);
+      parC ^= 1u;
+    } else {
+      CL::sync();
+    }
     if (dyn && round == 0) claimed = *CL::map(&s_claim, 0u);
     // 3a. FFT of the local slot columns (rows in natural order -> slot order)
     for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
@@ -751,13 +873,29 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
 #pragma unroll
       for (int p = 0; p < E; ++p) x[p] = sC[(p * L + l) * S::SCS + b];
       F::adj(x, l, tw, net);
+      if constexpr (XCH) {
+        const uint32_t lr = smem_addr(sR);
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int u = l + L * e;
-        CL::map(sR, (unsigned)(u / RN))[(u % RN) * S::SRS + c0 + b] = x[e];
+        for (int e = 0; e < E; ++e) {
+          const int u = l + L * e;
+          const uint32_t r = (uint32_t)(u / RN);
+          st_async2(map_rank(lr + 8u * (uint32_t)((u % RN) * S::SRS + c0 + b), r), x[e], map_rank(barR, r));
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int u = l + L * e;
+          CL::map(sR, (unsigned)(u / RN))[(u % RN) * S::SRS + c0 + b] = x[e];
+        }
       }
     }
-    CL::sync();
+    if constexpr (XCH) {
+      if (threadIdx.x == 0) xbar_expect(barR, (uint32_t)(8 * RN * N));  // every column of this CTA's rows
+      xbar_wait(barR, parR, a, xabort);
+      parR ^= 1u;
+    } else {
+      CL::sync();
+    }
     if (round == 0) flush_partials<NW>(sred, p.red);
     // 5. adjoint FFT of this CTA's rows and the object update
     for (int u0 = warp * G; u0 < RN; u0 += NW * G) {
