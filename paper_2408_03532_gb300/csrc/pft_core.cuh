@@ -164,4 +164,84 @@ struct Pft1D {
   }
 };
 
+// The same 1-D transform on 2P lanes (P <= 16): the two P-lane halves of the
+// group hold the same block and split the r terms between them, half h taking
+// j = h JH ... h JH + JH - 1 (JH = 7; half 1's seventh term is a zero pad).
+// Stage A runs in both halves; the lane network and the W' combine run on half
+// the terms each, and one shuffle across the halves adds the partial sums.
+template <int P, int Q, int MP>
+struct Pft1DSplit {
+  static_assert(P <= 16, "two halves of P lanes share a warp");
+  static constexpr int N = P * Q;
+  static constexpr int M = MP * P;
+  static constexpr int JH = (RMAX + 1) / 2;
+
+  // Forward: both halves hold x[Qk .. Qk+Q-1]; half h stores the outputs c of
+  // its residue with c % 2 == h.
+  template <class Store>
+  __device__ __forceinline__ static void forward(const float2 (&x)[Q], int k, int h,
+                                                 const float (&bh)[BH_ROWS][RMAX],
+                                                 const float2* __restrict__ sW,
+                                                 const LaneNet<P, false>& net, Store store) {
+    float2 C[RMAX];
+    stageA_fwd<Q>(x, C, bh);
+    float2 Ch[JH];
+#pragma unroll
+    for (int i = 0; i < JH; ++i) {
+      const float2 hi = (i + JH < RMAX) ? C[i + JH] : make_float2(0.f, 0.f);
+      Ch[i] = net.fwd(h ? hi : C[i]);
+    }
+    const int w = Pft1D<P, Q, MP>::first_out(k);
+    const int j0 = h * JH;
+#pragma unroll
+    for (int c = 0; c < MP; ++c) {
+      const int t = c * P + w;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < JH; ++i) {
+        const int j = min(j0 + i, RMAX - 1);  // half 1's pad term multiplies a zero
+        acc = cfma(acc, sW[j * M + t], Ch[i]);
+      }
+      acc.x += __shfl_xor_sync(PFT_FULL_MASK, acc.x, P);
+      acc.y += __shfl_xor_sync(PFT_FULL_MASK, acc.y, P);
+      if ((c & 1) == h) store(t, acc);
+    }
+  }
+
+  // Adjoint: both halves load the inputs of their residue and end with the
+  // whole x[l] = (A^H y)[Qk + l].
+  template <class Load>
+  __device__ __forceinline__ static void adjoint(Load load, int k, int h, const float (&bh)[BH_ROWS][RMAX],
+                                                 const float2* __restrict__ sW,
+                                                 const LaneNet<P, false>& net, float2 (&x)[Q]) {
+    const int w = Pft1D<P, Q, MP>::first_out(k);
+    float2 yv[MP];
+#pragma unroll
+    for (int c = 0; c < MP; ++c) yv[c] = load(c * P + w);
+    const int j0 = h * JH;
+    float2 Eh[JH];
+#pragma unroll
+    for (int i = 0; i < JH; ++i) {
+      const int j = min(j0 + i, RMAX - 1);
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc = cfmac(acc, sW[j * M + c * P + w], yv[c]);
+      Eh[i] = net.adj(acc);
+      if (j0 + i >= RMAX) Eh[i] = make_float2(0.f, 0.f);
+    }
+    float2 E[RMAX];
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+      const float2 mine = j < JH ? Eh[j] : Eh[j - JH];
+      E[j] = ((j < JH) == (h == 0)) ? mine : make_float2(0.f, 0.f);
+    }
+    stageA_adj<Q>(E, x, bh);
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      x[l].x += __shfl_xor_sync(PFT_FULL_MASK, x[l].x, P);
+      x[l].y += __shfl_xor_sync(PFT_FULL_MASK, x[l].y, P);
+    }
+  }
+};
+
 }  // namespace pftk

@@ -460,8 +460,11 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
                                                 const float2* __restrict__ gW, const float2* __restrict__ gtw) {
   using S = PiePftShape<P, Q, MP, C>;
   using T = Pft1D<P, Q, MP>;
+  using TS = Pft1DSplit<(P <= 16 ? P : 16), Q, MP>;
   using CL = Cluster<C>;
   constexpr int N = S::N, M = S::M, G = S::G, RN = S::RN, CM = S::CM, NW = NT / 32;
+  // every cluster size of a shape splits (or none does), so all launch forms round alike
+  constexpr bool SPLIT = (P == 16) && (MP == 2);
   extern __shared__ __align__(16) float2 sm[];
   float2* sW1 = sm + S::OFF_W1;
   float2* sW2 = sm + S::OFF_W2;
@@ -592,13 +595,23 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
       CL::sync();
     }
     if (dyn && round == 0) claimed = *CL::map(&s_claim, 0u);
-    // 3a. columns (axis 1) of this CTA's slice
-    for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
-      const int tl = cs0 + g;
-      float2 xv[Q];
+    // 3a. columns (axis 1) of this CTA's slice (SPLIT: one column per warp,
+    // its r terms split between the two 16-lane halves)
+    if constexpr (SPLIT) {
+      for (int tl = warp; tl < CM; tl += NW) {
+        float2 xv[Q];
 #pragma unroll
-      for (int l = 0; l < Q; ++l) xv[l] = sY[tl * S::SYT + Q * k + l + k];
-      T::forward(xv, k, c.bh[0], sW1, net, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
+        for (int l = 0; l < Q; ++l) xv[l] = sY[tl * S::SYT + Q * k + l + k];
+        TS::forward(xv, k, g, c.bh[0], sW1, net, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
+      }
+    } else {
+      for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
+        const int tl = cs0 + g;
+        float2 xv[Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) xv[l] = sY[tl * S::SYT + Q * k + l + k];
+        T::forward(xv, k, c.bh[0], sW1, net, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
+      }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -610,22 +623,32 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
     }
     warp_partial(round == 0 ? part : ResAcc<MODE>(0), sred);
     __syncthreads();
-    // 3c. adjoint columns -> row owners
-    for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
-      const int tl = cs0 + g;
+    // 3c. adjoint columns -> row owners (SPLIT: half g of the warp sends half
+    // of each block)
+    for (int cs0 = (SPLIT ? warp : warp * G); cs0 < CM; cs0 += (SPLIT ? NW : NW * G)) {
+      const int tl = SPLIT ? cs0 : cs0 + g;
       float2 xv[Q];
-      T::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, c.bh[0], sW1, net, xv);
+      if constexpr (SPLIT)
+        TS::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, g, c.bh[0], sW1, net, xv);
+      else
+        T::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, c.bh[0], sW1, net, xv);
       const int u0 = Q * k;
       const int tg = rank * CM + tl;
+      constexpr int L0 = SPLIT ? Q / 2 : Q;  // values each lane sends
+      const int lb = SPLIT ? g * (Q / 2) : 0;
+      float2 xs[L0];
+#pragma unroll
+      for (int l = 0; l < L0; ++l) xs[l] = (SPLIT && g) ? xv[(L0 + l) % Q] : xv[l];
       if constexpr (XCH) {
         const uint32_t r = (uint32_t)(u0 / RN);
         const uint32_t base = map_rank(smem_addr(sG), r), rb = map_rank(barG, r);
 #pragma unroll
-        for (int l = 0; l < Q; ++l) st_async2(base + 8u * (uint32_t)((u0 % RN + l) * S::SG + tg), xv[l], rb);
+        for (int l = 0; l < L0; ++l)
+          st_async2(base + 8u * (uint32_t)((u0 % RN + lb + l) * S::SG + tg), xs[l], rb);
       } else {
         float2* dst = CL::map(sG, (unsigned)(u0 / RN));
 #pragma unroll
-        for (int l = 0; l < Q; ++l) dst[(u0 % RN + l) * S::SG + tg] = xv[l];
+        for (int l = 0; l < L0; ++l) dst[(u0 % RN + lb + l) * S::SG + tg] = xs[l];
       }
     }
     if constexpr (XCH) {
