@@ -1435,10 +1435,16 @@ int batch_enqueue(pie_batch* b, const PieInstance* d_inst, void* const* objects,
       a.done = cl.d_done;
       a.ticket = cl.d_ticket;
       if (items > 0) {
-        // about twice the class's average parallelism (items over the longest
-        // chain): a class bound by one long chain holds a few clusters, not the
-        // GPU, while its persistent clusters wait
-        const long long par = (2LL * items + cl.chain - 1) / cl.chain;
+        // A fixed share of the GPU per class, so that the classes' persistent
+        // clusters do not crowd one another out: the batch takes at least as
+        // long as its longest colour chain, so a class whose chain is at least
+        // half the longest gets its average parallelism (items over its chain),
+        // and a class with a short chain only the clusters it needs to finish
+        // within the longest chain (items over that chain).
+        int chain_max = 1;
+        for (const pie_batch::Class& o : b->classes) chain_max = std::max(chain_max, o.chain);
+        const int span = 2 * cl.chain >= chain_max ? cl.chain : chain_max;
+        const long long par = ((long long)items + span - 1) / span;
         const int width = (int)std::min<long long>(cl.max_width, std::max<long long>(1, par));
         int rc = launch_pie_claimed(rep, transform, a, width, bs);
         if (rc != PFT_OK) return rc;
