@@ -447,6 +447,41 @@ int pie_batch_iteration(pie_batch* batch, void* const* objects, int transform, d
 int pie_batch_classes(const pie_batch* batch, int* nclasses, int* launches_per_sweep);
 int pie_batch_set_launch(pie_batch* batch, int form);
 
+/* ---- PIE over large frames ----------------------------------------------
+ * Section 4's large-scale regime (frames of n = 2048 ... 16384 pixels a side,
+ * M = 128): the PFT sweeps of Algorithm 3's warm-start phase (Eq. pie_update
+ * with the PFT of Algorithm 5 and reading R4 for its inverse), coloured, on
+ * the split-BF16 large-frame transforms. Each colour's positions (disjoint
+ * patches) are one batch: exit waves w . Q_j z, pft_forward, the modulus
+ * projection onto the cropped amplitudes, pft_adjoint, and the object update
+ * beta conj(w) / (max|w|^2 n^2) A^H R. A sweep is sequential PIE in
+ * colour-major order (greedy colouring in index order, as pie_scan_schedule).
+ * The full-FFT refine phase is not built for these sizes.
+ *
+ * pie_lf_create(out, problem, probe, positions, intensities, stream)
+ *   problem: as for pie_ctx_create; mode must be PIE_MODE_COLOURED, the
+ *   object width even, n and M a large-frame shape pft_plan_create builds in
+ *   PFT_PREC_SPLIT_BF16 (n = 2048 ... 16384, M = 128), else UNSUPPORTED.
+ *   probe: device [n][n] complex (copied); positions: host int32 [N][2]
+ *   (row, col), patches inside the object, every col even (INVALID_ARG
+ *   otherwise); intensities: device float [N][n][n] in FFT order, of which
+ *   only the centred M x M crop is kept (sqrt taken); a NaN or infinite value
+ *   returns PFT_ERR_NONFINITE. Synchronises `stream`.
+ * pie_lf_iteration(ctx, object, beta, stats, stream)
+ *   one PFT sweep in place on `object` (device [obj_h][obj_w] complex,
+ *   16-byte aligned). With `stats` the call synchronises and fills Phi (Eq. 4
+ *   by R12) and the relative change (allocating one object-sized copy on
+ *   first use); NONFINITE for a non-finite objective or change.
+ * pie_lf_colours(ctx, ncolours, max_colour): colours and the largest colour.
+ */
+typedef struct pie_lf pie_lf;
+
+int pie_lf_create(pie_lf** out, const pie_problem* problem, const void* probe, const int32_t* positions,
+                  const float* intensities, void* stream);
+int pie_lf_destroy(pie_lf* ctx);
+int pie_lf_iteration(pie_lf* ctx, void* object, double beta, pie_stats* stats, void* stream);
+int pie_lf_colours(const pie_lf* ctx, int* ncolours, int* max_colour);
+
 /* ---- allocation-free error reduction ------------------------------------
  * The paper has no counterpart to this call. It exists for callers that cannot
  * call cudaMalloc when they need the error: plug-ins inside a host framework

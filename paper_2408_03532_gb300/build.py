@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libpft_gb300.so")
 
-CU_SOURCES = ["api.cu", "plan.cu", "fft.cu", "pie.cu", "pie_pft.cu", "pie_full.cu", "noalloc.cu", "pft_tc.cu", "pft_tc64.cu", "pft_tc_adj.cu", "pft_tc64_adj.cu", "pft_lf.cu"]
+CU_SOURCES = ["api.cu", "plan.cu", "fft.cu", "pie.cu", "pie_pft.cu", "pie_full.cu", "pie_lf.cu", "noalloc.cu", "pft_tc.cu", "pft_tc64.cu", "pft_tc_adj.cu", "pft_tc64_adj.cu", "pft_lf.cu"]
 CPP_SOURCES = ["coeffs.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

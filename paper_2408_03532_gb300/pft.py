@@ -122,6 +122,10 @@ def load() -> ctypes.CDLL:
         "pie_ctx_test_unreachable_wait": (ctypes.c_int, [_P, ctypes.c_int]),
         "pie_amp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
+        "pie_lf_create": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+        "pie_lf_destroy": (ctypes.c_int, [_P]),
+        "pie_lf_iteration": (ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P]),
+        "pie_lf_colours": (ctypes.c_int, [_P, _P, _P]),
         "pie_batch_create": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
         "pie_batch_destroy": (ctypes.c_int, [_P]),
         "pie_batch_iteration": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _P, _P]),
@@ -464,6 +468,52 @@ class PieContext:
     def close(self):
         if getattr(self, "_h", None):
             load().pie_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LargeFramePie:
+    """PFT sweeps of PIE over large frames (n = 2048 ... 16384, M = 128): each
+    colour's positions are one batch of the split-BF16 large-frame transforms."""
+
+    def __init__(self, obj_shape, probe, positions, intensities, M: int = 128, p: int = 0, eps: float = 1e-7,
+                 stream=None):
+        import torch
+        n = probe.shape[-1]
+        _need(probe, torch.complex64, (n, n), "probe")
+        _need(intensities, torch.float32, (n, n), "intensities")
+        pos = np.ascontiguousarray(np.asarray(positions, dtype=np.int32).reshape(-1, 2))
+        prob = PieProblem(int(obj_shape[0]), int(obj_shape[1]), n, len(pos), M, p, eps, MODE_COLOURED, PATH_AUTO,
+                          1e-3, 0)
+        h = ctypes.c_void_p()
+        _check(load().pie_lf_create(ctypes.byref(h), ctypes.byref(prob), _ptr(probe), pos.ctypes.data,
+                                    _ptr(intensities), _stream(stream)))
+        self._h = h
+        self.shape = (int(obj_shape[0]), int(obj_shape[1]))
+        self.n, self.M, self.npos = n, M, len(pos)
+
+    def colours(self) -> tuple[int, int]:
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load().pie_lf_colours(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def iteration(self, obj, beta: float = 1.0, stats: bool = True, stream=None):
+        """One PFT sweep over all positions, in place on obj."""
+        import torch
+        _need(obj, torch.complex64, self.shape, "object")
+        st = PieStats()
+        _check(load().pie_lf_iteration(self._h, _ptr(obj), beta, ctypes.byref(st) if stats else None,
+                                       _stream(stream)))
+        return {"phi": st.phi, "rel_change": st.rel_change} if stats else None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pie_lf_destroy(self._h)
             self._h = None
 
     def __del__(self):

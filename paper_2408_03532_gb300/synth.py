@@ -64,6 +64,35 @@ def make_object(side: int, seed: int = SEED_OBJECT, sigma: float = 2.0) -> np.nd
     return amp * np.exp(1j * pha)
 
 
+def make_object_torch(side: int, device, seed: int = SEED_OBJECT, sigma: float = 2.0):
+    """The make_object recipe drawn and smoothed with torch on `device` (complex64),
+    for objects too large for the numpy route (the 16384^2 large-scale workload):
+    uniform noise, a separable Gaussian of sigma px truncated at 4 sigma with
+    reflecting edges, min-max to amplitude [0.5, 1] and phase [-pi/2, pi/2]. Same
+    distribution as make_object, not the same draw."""
+    import torch
+    import torch.nn.functional as F
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    rad = int(4.0 * sigma + 0.5)
+    x = torch.arange(-rad, rad + 1, device=device, dtype=torch.float32)
+    k = torch.exp(-0.5 * (x / sigma) ** 2)
+    k = k / k.sum()
+
+    def smooth(a):
+        a = a[None, None]
+        a = F.conv2d(F.pad(a, (rad, rad, 0, 0), mode="reflect"), k.view(1, 1, 1, -1))
+        a = F.conv2d(F.pad(a, (0, 0, rad, rad), mode="reflect"), k.view(1, 1, -1, 1))
+        return a[0, 0]
+
+    def minmax(a, lo, hi):
+        return lo + (hi - lo) * (a - a.min()) / (a.max() - a.min())
+
+    amp = minmax(smooth(torch.rand(side, side, generator=g, device=device)), 0.5, 1.0)
+    pha = minmax(smooth(torch.rand(side, side, generator=g, device=device)), -math.pi / 2, math.pi / 2)
+    return torch.polar(amp, pha)
+
+
 def make_probe(n: int, seed: int = SEED_PROBE, radius: float | None = None,
                edge: float = 2.0) -> np.ndarray:
     """Disc probe with a Gaussian edge and a random quadratic phase (complex128 [n, n])."""

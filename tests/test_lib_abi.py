@@ -97,6 +97,9 @@ def test_null_and_invalid_arguments_are_refused_before_any_gpu_work(lib):
         lambda: lib.pie_batch_iteration(null, null, 0, 1.0, null, null),
         lambda: lib.pie_batch_classes(null, null, null),
         lambda: lib.pie_batch_set_launch(null, 0),
+        lambda: lib.pie_lf_create(ctypes.byref(out), null, null, null, null, null),
+        lambda: lib.pie_lf_iteration(null, null, 1.0, null, null),
+        lambda: lib.pie_lf_colours(null, null, null),
     ]
     for i, call in enumerate(calls):
         assert call() == -1, i

@@ -83,3 +83,20 @@ def test_start_frames_and_batch_recipe():
         assert sp["side"] in (256, 512, 1024, 2048) and sp["n"] in (64, 128, 256)
         assert sp["n"] < sp["side"] and sp["M"] in (16, 32, 64) and sp["M"] <= sp["n"]
         assert 50 <= sp["npos"] <= 2000
+
+
+def test_torch_object_recipe():
+    """The torch version of the object recipe (for the 16384^2 workload): the same
+    ranges, a smooth field (neighbouring pixels close, as after a sigma = 2 px
+    Gaussian), and the same draw for the same seed."""
+    torch = pytest.importorskip("torch")
+    a = synth.make_object_torch(256, "cpu")
+    b = synth.make_object_torch(256, "cpu")
+    assert a.dtype == torch.complex64 and torch.equal(a, b)
+    amp, pha = a.abs(), a.angle()
+    assert abs(amp.min().item() - 0.5) < 1e-5 and abs(amp.max().item() - 1.0) < 1e-5
+    assert abs(pha.min().item() + np.pi / 2) < 1e-5 and abs(pha.max().item() - np.pi / 2) < 1e-5
+    step = (amp[:, 1:] - amp[:, :-1]).abs().mean().item()
+    ref = np.abs(np.diff(np.abs(synth.make_object(256)), axis=1)).mean()
+    assert 0.5 * ref < step < 2.0 * ref
+    assert not torch.equal(a, synth.make_object_torch(256, "cpu", seed=9))
