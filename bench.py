@@ -319,6 +319,7 @@ def main() -> None:
     ap.add_argument("--pft-frames", type=int, default=4096)
     ap.add_argument("--no-batch64", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the amplitude-loss gradient timing")
+    ap.add_argument("--no-pie-large", action="store_true", help="skip the large-frame PIE sweep timing")
     ap.add_argument("--sweep-launch", choices=["auto", "dataflow", "persistent", "per-colour"], default="auto",
                     help="coloured sweeps as one cooperative launch (per-position waits on overlapping "
                          "predecessors, or a grid barrier per colour) or one launch per colour (auto: the "
@@ -464,6 +465,7 @@ def main() -> None:
     pft_batch = None if args.no_pft_batch else measure_pft_batch(pft, torch, dev, stream, flush, args.pft_frames)
     batch64 = None if args.no_batch64 else measure_batch64(pft, synth, torch, dev, stream, flush)
     grad = None if args.no_grad else measure_grad(pft, synth, torch, dev, stream, flush)
+    pie_large = None if args.no_pie_large else measure_pie_large(pft, synth, torch, dev, stream, flush)
     pft_large = None if args.no_pft_large else measure_pft_large(pft, torch, dev, stream, flush,
                                                                  _cases(args.pft_large_cases))
 
@@ -504,7 +506,7 @@ def main() -> None:
                         "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
                 "gpu_launches": sum(launches_per_sweep) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "time_to_target": ttt, "grad_c3": grad, "pft_batch": pft_batch, "pft_large": pft_large, "batch64": batch64, "wall_s": wall, "colours": ncol,
+                "time_to_target": ttt, "grad_c3": grad, "pie_large": pie_large, "pft_batch": pft_batch, "pft_large": pft_large, "batch64": batch64, "wall_s": wall, "colours": ncol,
                 "autotune": tuning}
         print(json.dumps(line))
     if world > 1:
@@ -597,19 +599,24 @@ def measure_pft_batch(pft, torch, dev, stream, flush, frames: int = 4096, n: int
 # DRAM traffic (read + write bytes per frame) of the split-BF16 kernels from
 # ncu captures, each valid only for the source file it was taken on.
 TC_TRAFFIC = {
-    # 4096 frames of 256 x 256; median of 6 / 7 launches (one ncu pass each)
+    # 512 frames of 256 x 256 (256 MB, twice the L2), one kernel and three launches per capture
+    # (`bench.py --only-pft-batch --pft-frames 512`, ncu -s 2 -c 3, dram__bytes_read/write), median
+    # launch. Forwards: scaled per frame (the frames are read once; their 4-8 MB of outputs stay in
+    # L2). Adjoints: reads scaled per frame; of the 268 MB written, a fixed L2-resident tail
+    # (written minus counted: 65 MB) is still dirty when the launch ends, at 4096 frames as at 512, so
+    # the full-size writes are the output less that tail
     "k_pft_tc_fwd": {"source": "pft_tc.cu",
                      "source_sha256": "e9cda75fbc3b27ecc1405097e3681af2dc09b650905fd4ee4102100457d2df1d",
-                     "bytes_per_frame": (2147662336 + 29972608) / 4096},
+                     "bytes_per_frame": (268566016 + 124160) / 512},
     "k_pft_tc_adj": {"source": "pft_tc_adj.cu",
                      "source_sha256": "e3d99338b748ea0a4d4b0ce7b38083d91766084346370a63963eba7c5346de3e",
-                     "bytes_per_frame": (33716480 + 2082690560) / 4096},
+                     "read_per_frame": 4327168 / 512, "l2_tail": 512 * 524288 - 203225088},
     "k_pft_tc64_fwd": {"source": "pft_tc64.cu",
                        "source_sha256": "5fcaf83cb9ebd00ada031dd48effd9652351ff3f29e1b6f6e2eee59c7651baaf",
-                       "bytes_per_frame": (2149662464 + 124201856) / 4096},
+                       "bytes_per_frame": (268773632 + 4632832) / 512},
     "k_pft_tc64_adj": {"source": "pft_tc64_adj.cu",
                        "source_sha256": "d9af80253fb834e09a235ebe347ee3689edac01c8f29a5eab02ad3454ddbb784",
-                       "bytes_per_frame": (134392576 + 2082455296) / 4096},
+                       "read_per_frame": 16924416 / 512, "l2_tail": 512 * 524288 - 202724608},
 }
 
 def _csrc_sha(name: str) -> str:
@@ -631,10 +638,10 @@ def _csrc_sha(name: str) -> str:
 # writes are the L2's write-back of object lines. Valid only for the sources
 # hashed below (None otherwise).
 PIE_TRAFFIC = {
-    "pie_pft": {"sources": {"pie_kernels.cuh": "4c1d9a69170bdf40f5560292d9d84d2d0bfaaa72ff0277da60460241cc03699c",
-                            "pft_core.cuh": "4dfa31346e0ac684953fa89ce8271d10337e260a8ecc858bb0f8b85d03925495",
+    "pie_pft": {"sources": {"pie_kernels.cuh": "1e33f60d62c243867ee1b6c416eadca240b0b9af53f124e26dc7cb64afc2a862",
+                            "pft_core.cuh": "64b36f8b6ff3b2f453a06f28a26ee6ce1bbc559b067129de36559fc797c8b43f",
                             "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
-                "read_per_position": 3328 / 128, "write_per_position": 1179904 / 128},
+                "read_per_position": 5888 / 128, "write_per_position": 1143040 / 128},
     "pie_full": {"sources": {"pie_kernels.cuh": "4c1d9a69170bdf40f5560292d9d84d2d0bfaaa72ff0277da60460241cc03699c",
                              "fft_core.cuh": "dd2552f57edd2220bfec6952833eeb81f9edcb4dd2d2b1e7f4bd407c1bbe064a",
                              "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
@@ -651,13 +658,15 @@ def _pie_traffic(kernel: str, positions: int):
     return (rec["read_per_position"] + rec["write_per_position"]) * positions
 
 
-def _traffic(kernel: str, frames: int):
+def _traffic(kernel: str, frames: int, n: int = 256):
+    """DRAM bytes of one launch over `frames` frames from the stored capture, or
+    None when the source changed since it was taken."""
     rec = TC_TRAFFIC.get(kernel)
-    if rec is None:
+    if rec is None or rec["source_sha256"] != _csrc_sha(rec["source"]):
         return None
-    if rec["bytes_per_frame"] and rec["source_sha256"] == _csrc_sha(rec["source"]):
+    if "bytes_per_frame" in rec:
         return rec["bytes_per_frame"] * frames
-    return None
+    return rec["read_per_frame"] * frames + max(0, 8 * n * n * frames - rec["l2_tail"])
 
 
 def measure_split_bf16(pft, torch, plan32, x, y32, timed, byts, peak, kind, fp32_fwd_ms, fp32_adj_ms,
@@ -756,6 +765,66 @@ def measure_pft_large(pft, torch, dev, stream, flush, cases=((8192, 4), (16384, 
         del x, y, xa, ref, plan
         torch.cuda.empty_cache()
     return out
+
+
+def measure_pie_large(pft, synth, torch, dev, stream, flush, reps: int = 3) -> dict:
+    """Section 4's large-scale non-blind workload: a 16384^2 object, 3 x 3
+    windows of 8192^2 (stride 4096), M = 128 (m~ = p = 64, r = 13), noise-free
+    data: one PFT sweep of the warm-start phase through the large-frame PIE
+    context (colours as batches of the split-BF16 large-frame transforms),
+    CUDA events, L2 flushed before each sweep. Algorithmic HBM bytes per
+    position: the exit wave reads patch and probe and writes the frame, the
+    forward reads it, the adjoint writes it, the update reads frame, probe and
+    patch and writes the patch: 10 x 8 n^2."""
+    side, n, M = 16384, 8192, 128
+    obj = synth.make_object_torch(side, dev)
+    probe = torch.from_numpy(synth.make_probe(n).astype(np.complex64)).to(dev)
+    pos = synth.raster_scan(3, 3, 4096, 0)
+    inten = synth.simulate_intensities_torch(obj, probe, pos, chunk=3)
+    ctx = pft.LargeFramePie((side, side), probe, pos, inten, M=M)
+    del inten
+    torch.cuda.empty_cache()
+    z = torch.polar(torch.rand(side, side, device=dev, generator=torch.Generator(device=dev).manual_seed(5)),
+                    (math.pi / 2) * torch.rand(side, side, device=dev,
+                                               generator=torch.Generator(device=dev).manual_seed(6)))
+    ctx.iteration(z, 1.0, stats=False)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.iteration(z, 1.0, stats=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    st = ctx.iteration(z, 1.0, stats=True)
+    ncol, maxcol = ctx.colours()
+    ctx.close()
+    ms = statistics.median(ts)
+    # context: the full 2-D FFT and its inverse of one window (cuFFT through torch), the transform
+    # pair a full-FFT (refine-phase) update needs per position
+    fr = probe.clone()
+    torch.fft.ifft2(torch.fft.fft2(fr))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    a.record(stream)
+    torch.fft.ifft2(torch.fft.fft2(fr))
+    b.record(stream)
+    torch.cuda.synchronize()
+    fft_pair_ms = a.elapsed_time(b)
+    del fr
+    byts = 10 * 8 * n * n * len(pos)
+    peak, kind = hbm_peak()
+    del obj, z, probe
+    torch.cuda.empty_cache()
+    return {"workload": "16384^2 object, 3 x 3 windows of 8192^2 (stride 4096), M = 128, noise-free, split-BF16",
+            "pft_sweep_ms": ms, "frames_per_s": len(pos) / (ms / 1e3), "colours": ncol, "largest_colour": maxcol,
+            "phi_after": st["phi"], "rel_change": st["rel_change"],
+            "cufft_pair_ms_per_window": fft_pair_ms,
+            "cufft_pairs_per_sweep_ms": fft_pair_ms * len(pos),
+            "roofline": {"bound": "hbm", "achieved": byts / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": byts / (ms / 1e3) / 1e9 / peak, "peak_kind": kind,
+                         "algorithmic_bytes": byts}}
 
 
 def measure_grad(pft, synth, torch, dev, stream, flush, reps: int = 10) -> dict:
