@@ -394,6 +394,16 @@ int pie_ctx_test_unreachable_wait(pie_ctx* ctx, int kind);
  * launch per colour (pie_ctx_info_get shows it). */
 int pie_ctx_set_persistent(pie_ctx* ctx, int transform, int persistent);
 
+/* Cluster size (CTAs per position: 1, 2, 4 or 8) of `transform`'s sweeps in
+ * the context's mode, in every launch form, in place of the autotuner's or
+ * the built-in choice (largest size whose clusters for a whole colour fit on
+ * the GPU at once); 0 returns to the built-in choice. The result of a sweep
+ * does not depend on it beyond the rounding of the FP32 transforms (the
+ * rows, columns and reductions are split differently over the CTAs).
+ * INVALID_ARG for another value; UNSUPPORTED when no kernel of that size is
+ * built for the context's (n, M) and mode. Synchronises the device. */
+int pie_ctx_set_cluster(pie_ctx* ctx, int transform, int cluster);
+
 /* Phase-aligned error min_phi ||e^{i phi} z - truth|| / ||truth|| over the
  * context's illuminated mask (FP64 on the GPU); synchronises `stream`. */
 int pie_nrmse(pie_ctx* ctx, const void* object, const void* truth, double* out, void* stream);

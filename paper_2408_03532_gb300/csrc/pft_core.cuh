@@ -244,4 +244,114 @@ struct Pft1DSplit {
   }
 };
 
+// The same 1-D transform on 32 lanes for P = 8: four 8-lane groups hold the
+// same block and take four of the r terms each (group h: j = 4h .. 4h + 3;
+// j >= r are zero pads), in stage A, the lane network and the W' sums; two
+// shuffles across the groups add the partial sums. B comes from shared memory
+// (sB[l * RMAX + j], rows l = 0 .. Q/2) because each group reads other terms.
+template <int Q, int MP>
+struct Pft1DSplit4 {
+  static constexpr int P = 8;
+  static constexpr int N = P * Q;
+  static constexpr int M = MP * P;
+  static constexpr int JH = 4;
+
+  // Forward: every group holds x[Qk .. Qk+Q-1]; group h stores output c = h.
+  template <class Store>
+  __device__ __forceinline__ static void forward(const float2 (&x)[Q], int k, int h, const float* __restrict__ sB,
+                                                 const float2* __restrict__ sW, const LaneNet<P, false>& net,
+                                                 Store store) {
+    constexpr int H = Q / 2;
+    float2 s[H > 1 ? H : 1], d[H > 1 ? H : 1];
+#pragma unroll
+    for (int l = 1; l < H; ++l) {
+      s[l] = cadd(x[l], x[Q - l]);
+      d[l] = csub(x[l], x[Q - l]);
+    }
+    const int j0 = JH * h;  // even, so the parity of j is the parity of i
+    float2 C[JH];
+#pragma unroll
+    for (int i = 0; i < JH; ++i) {
+      const int j = min(j0 + i, RMAX - 1);
+      float2 acc = cscale(x[0], sB[j]);
+      if ((i & 1) == 0) {  // abscissa 0 (row Q/2) contributes to j = 0 only: B[Q/2][j] = a_j 0^j
+        const float b = sB[H * RMAX + j];
+        acc.x = fmaf(b, x[H].x, acc.x);
+        acc.y = fmaf(b, x[H].y, acc.y);
+      }
+#pragma unroll
+      for (int l = 1; l < H; ++l) {
+        const float b = sB[l * RMAX + j];
+        const float2 v = (i & 1) ? d[l] : s[l];
+        acc.x = fmaf(b, v.x, acc.x);
+        acc.y = fmaf(b, v.y, acc.y);
+      }
+      const float2 v = net.fwd(acc);
+      C[i] = (j0 + i < RMAX) ? v : make_float2(0.f, 0.f);
+    }
+    const int w = Pft1D<P, Q, MP>::first_out(k);
+#pragma unroll
+    for (int c = 0; c < MP; ++c) {
+      const int t = c * P + w;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < JH; ++i) acc = cfma(acc, sW[min(j0 + i, RMAX - 1) * M + t], C[i]);
+#pragma unroll
+      for (int o = 8; o <= 16; o <<= 1) {
+        acc.x += __shfl_xor_sync(PFT_FULL_MASK, acc.x, o);
+        acc.y += __shfl_xor_sync(PFT_FULL_MASK, acc.y, o);
+      }
+      if (c == h) store(t, acc);
+    }
+  }
+
+  // Adjoint: every group loads the inputs of its residue; group h ends with
+  // xq[i] = (A^H y)[Qk + h Q/4 + i], a quarter of the block.
+  template <class Load>
+  __device__ __forceinline__ static void adjoint(Load load, int k, int h, const float* __restrict__ sB,
+                                                 const float2* __restrict__ sW, const LaneNet<P, false>& net,
+                                                 float2 (&xq)[Q / 4]) {
+    constexpr int H = Q / 2, QQ = Q / 4;
+    const int w = Pft1D<P, Q, MP>::first_out(k);
+    float2 yv[MP];
+#pragma unroll
+    for (int c = 0; c < MP; ++c) yv[c] = load(c * P + w);
+    const int j0 = JH * h;
+    float2 E[JH];
+#pragma unroll
+    for (int i = 0; i < JH; ++i) {
+      const int jj = min(j0 + i, RMAX - 1);
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < MP; ++c) acc = cfmac(acc, sW[jj * M + c * P + w], yv[c]);
+      const float2 v = net.adj(acc);
+      E[i] = (j0 + i < RMAX) ? v : make_float2(0.f, 0.f);
+    }
+    // every term's E from its group (lane k of group g holds terms 4g .. 4g + 3)
+    float2 Ea[4 * JH];
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+      for (int i = 0; i < JH; ++i) {
+        Ea[JH * g + i].x = __shfl_sync(PFT_FULL_MASK, E[i].x, k + 8 * g);
+        Ea[JH * g + i].y = __shfl_sync(PFT_FULL_MASK, E[i].y, k + 8 * g);
+      }
+    // x[l] = sum_j B[l][j] E[j]; B[Q - l][j] = (-1)^j B[l][j]
+#pragma unroll
+    for (int i = 0; i < QQ; ++i) {
+      const int l = h * QQ + i;
+      const bool up = l > H;
+      const float* row = sB + (up ? Q - l : l) * RMAX;
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        const float b = (up && (j & 1)) ? -row[j] : row[j];
+        acc.x = fmaf(b, Ea[j].x, acc.x);
+        acc.y = fmaf(b, Ea[j].y, acc.y);
+      }
+      xq[i] = acc;
+    }
+  }
+};
+
 }  // namespace pftk

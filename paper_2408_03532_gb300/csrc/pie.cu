@@ -1166,6 +1166,28 @@ int pie_ctx_set_persistent(pie_ctx* c, int transform, int persistent) {
   return PFT_OK;
 }
 
+int pie_ctx_set_cluster(pie_ctx* c, int transform, int cluster) {
+  if (!c) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
+  if (transform != PIE_TRANSFORM_PFT && transform != PIE_TRANSFORM_FULL)
+    return pfth::set_error(PFT_ERR_INVALID_ARG, "unknown transform %d", transform);
+  const int t = transform == PIE_TRANSFORM_PFT ? 0 : 1;
+  const int mode = c->pb.mode == PIE_MODE_COLOURED ? MODE_COLOURED : MODE_BATCHED;
+  int q = -1;
+  if (cluster != 0) {
+    for (int i = 0; i < 4; ++i)
+      if (cluster == 1 << i) q = i;
+    if (q < 0) return pfth::set_error(PFT_ERR_INVALID_ARG, "cluster size %d is not 0, 1, 2, 4 or 8", cluster);
+    if (!c->kern[t][mode][q].fn)
+      return pfth::set_error(PFT_ERR_UNSUPPORTED, "no %d-CTA PIE kernel for this n, M and mode", cluster);
+  }
+  PFT_CUDA_TRY(cudaDeviceSynchronize());
+  c->tuned[t][mode] = q;
+  if (mode == MODE_COLOURED) c->flow_ci[t] = q;
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);  // captured sweeps hold the launch shape
+  c->graphs.clear();
+  return PFT_OK;
+}
+
 int pie_ctx_test_unreachable_wait(pie_ctx* c, int kind) {
   if (!c) return pfth::set_error(PFT_ERR_INVALID_ARG, "null argument");
   if (kind < PIE_TEST_WAIT_NONE || kind > PIE_TEST_WAIT_DATAFLOW)

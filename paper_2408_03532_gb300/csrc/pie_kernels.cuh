@@ -432,8 +432,14 @@ struct PiePftShape {
   static constexpr int N = P * Q, M = MP * P, G = 32 / P;
   static constexpr int RN = N / C;   // rows owned by one CTA
   static constexpr int CM = M / C;   // columns owned by one CTA
+  // P = 8, Q >= 16: four 8-lane groups share each column transform, one column
+  // per warp. Without it a warp runs G = 4 columns and a CTA needs CM % 4 == 0,
+  // so the few columns of a small-M frame sit on one warp. With Q = 16 the
+  // 8-CTA cluster (two columns per CTA) is still left out: its exchange costs
+  // more than the column phase it shortens.
+  static constexpr bool SPLIT4 = (P == 8) && (MP == 2) && (Q >= 16);
   static constexpr bool VALID = (N % C == 0) && (M % C == 0) && CM >= 1 && (RN % G == 0) &&
-                                (CM % G == 0) && (RN % Q == 0);
+                                ((SPLIT4 && Q >= 32) || CM % G == 0) && (RN % Q == 0);
   // column slice of Y, all rows: element (t, u) at t * SYT + u + u / Q
   static constexpr int SYT_BASE = N + N / Q;
   static constexpr int SYT = SYT_BASE + (((8 - SYT_BASE % 16) + 16) % 16);
@@ -449,7 +455,9 @@ struct PiePftShape {
   static constexpr int OFF_Z = (C == 1) ? OFF_Y + (Y_SIZE > G_SIZE ? Y_SIZE : G_SIZE) : OFF_G + G_SIZE;
   static constexpr int OFF_RED = OFF_Z + M * ZS;
   static constexpr int OFF_D = OFF_RED + 16;           // amplitudes of the CTA's columns: [M][CM] floats
-  static constexpr size_t SMEM = sizeof(float2) * (OFF_D + (M * CM + 1) / 2);
+  static constexpr int OFF_BH = OFF_D + (M * CM + 1) / 2;  // SPLIT4: axis-1 B rows 0 .. Q/2 [Q/2 + 1][RMAX] floats
+  static constexpr int BH_SIZE = SPLIT4 ? ((Q / 2 + 1) * RMAX + 1) / 2 : 0;
+  static constexpr size_t SMEM = sizeof(float2) * (OFF_BH + BH_SIZE);
 };
 
 // CLAIM: the variant whose clusters claim items from PieArgs::ticket (dataflow
@@ -461,8 +469,10 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
   using S = PiePftShape<P, Q, MP, C>;
   using T = Pft1D<P, Q, MP>;
   using TS = Pft1DSplit<(P <= 16 ? P : 16), Q, MP>;
+  using TS4 = Pft1DSplit4<Q, MP>;
   using CL = Cluster<C>;
   constexpr int N = S::N, M = S::M, G = S::G, RN = S::RN, CM = S::CM, NW = NT / 32;
+  constexpr bool SPLIT4 = S::SPLIT4;
   // every cluster size of a shape splits (or none does), so all launch forms round alike
   constexpr bool SPLIT = (P == 16) && (MP == 2);
   extern __shared__ __align__(16) float2 sm[];
@@ -474,11 +484,14 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
   float2* sZ = sm + S::OFF_Z;
   double* sred = reinterpret_cast<double*>(sm + S::OFF_RED);
   float* sD = reinterpret_cast<float*>(sm + S::OFF_D);
+  float* sBh = reinterpret_cast<float*>(sm + S::OFF_BH);
   if (!cluster_shape_ok<C>(a.gstatus)) return;
   const unsigned rank = CL::rank();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = lane % P, g = lane / P;
   const int r0 = rank * RN;
+  if constexpr (SPLIT4)  // made visible by the cluster barrier before the first item
+    for (int i = threadIdx.x; i < (Q / 2 + 1) * RMAX; i += NT) sBh[i] = c.bh[0][i / RMAX][i % RMAX];
   // With one row group per warp, the probe and patch values of the warp's rows
   // stay in registers from the exit wave to the update, and the next work
   // item's are loaded as soon as the current one is done.
@@ -604,6 +617,13 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
         for (int l = 0; l < Q; ++l) xv[l] = sY[tl * S::SYT + Q * k + l + k];
         TS::forward(xv, k, g, c.bh[0], sW1, net, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
       }
+    } else if constexpr (SPLIT4) {
+      for (int tl = warp; tl < CM; tl += NW) {
+        float2 xv[Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) xv[l] = sY[tl * S::SYT + Q * k + l + k];
+        TS4::forward(xv, k, g, sBh, sW1, net, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
+      }
     } else {
       for (int cs0 = warp * G; cs0 < CM; cs0 += NW * G) {
         const int tl = cs0 + g;
@@ -624,7 +644,26 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
     warp_partial(round == 0 ? part : ResAcc<MODE>(0), sred);
     __syncthreads();
     // 3c. adjoint columns -> row owners (SPLIT: half g of the warp sends half
-    // of each block)
+    // of each block; SPLIT4: group g computes and sends a quarter of it)
+    if constexpr (SPLIT4) {
+      for (int tl = warp; tl < CM; tl += NW) {
+        float2 xq[Q / 4];
+        TS4::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, g, sBh, sW1, net, xq);
+        const int u0 = Q * k + g * (Q / 4);
+        const int tg = rank * CM + tl;
+        if constexpr (XCH) {
+          const uint32_t r = (uint32_t)(u0 / RN);
+          const uint32_t base = map_rank(smem_addr(sG), r), rb = map_rank(barG, r);
+#pragma unroll
+          for (int l = 0; l < Q / 4; ++l)
+            st_async2(base + 8u * (uint32_t)((u0 % RN + l) * S::SG + tg), xq[l], rb);
+        } else {
+          float2* dst = CL::map(sG, (unsigned)(u0 / RN));
+#pragma unroll
+          for (int l = 0; l < Q / 4; ++l) dst[(u0 % RN + l) * S::SG + tg] = xq[l];
+        }
+      }
+    } else
     for (int cs0 = (SPLIT ? warp : warp * G); cs0 < CM; cs0 += (SPLIT ? NW : NW * G)) {
       const int tl = SPLIT ? cs0 : cs0 + g;
       float2 xv[Q];

@@ -120,6 +120,7 @@ def load() -> ctypes.CDLL:
         "pie_ctx_set_order": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "pie_ctx_set_persistent": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
         "pie_ctx_test_unreachable_wait": (ctypes.c_int, [_P, ctypes.c_int]),
+        "pie_ctx_set_cluster": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
         "pie_amp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
         "pie_nrmse_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
         "pie_lf_create": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -403,6 +404,11 @@ class PieContext:
         per-position waits on overlapping predecessors)."""
         form = int(persistent) if not isinstance(persistent, bool) else (1 if persistent else 0)
         _check(load().pie_ctx_set_persistent(self._h, transform, form))
+
+    def set_cluster(self, transform: int, cluster: int):
+        """CTAs per position (1, 2, 4, 8) for `transform`'s sweeps in every
+        launch form; 0 returns to the built-in choice."""
+        _check(load().pie_ctx_set_cluster(self._h, transform, int(cluster)))
 
     def test_unreachable_wait(self, kind: int):
         """Test hook: TEST_WAIT_GRID_BARRIER / TEST_WAIT_DATAFLOW make every

@@ -599,3 +599,39 @@ def test_full_sweep_256_matches_oracle(env, form):
     ctx.iteration(z, tr, 0.8, mode=pft.MODE_BATCHED)
     zb, _ = opie.batched_sweep(start.astype(np.complex128), P["probe"], P["pos"], d, T, 0.8, delta_rel=1e-3)
     assert rel(z.cpu().numpy(), zb) < TOL
+
+
+@pytest.mark.parametrize("n,M", [(256, 16), (128, 16), (64, 16), (128, 32)])
+def test_every_cluster_size_matches_oracle(env, n, M):
+    """Each built cluster size of the PFT-PIE kernel (the p = 8 shapes with
+    Q >= 16 share each column transform among four 8-lane groups; n = 64,
+    M = 16 does not) in the per-colour and dataflow forms: two coloured sweeps
+    against the oracle. A size that is not built is refused."""
+    torch, pft = env
+    P = synth.spiral_problem(side=2 * n + 64, n=n, count=30, peak_photons=1e4, M=M)
+    ctx = make_ctx(P, torch, pft)
+    tr = pft.TRANSFORM_PFT
+    order = opie.colour_major_order(ctx.colours().astype(np.int64))
+    T, d = oracle_T(P, "pft")
+    zo = P["init"].astype(np.complex128)
+    for _ in range(2):
+        zo, _ = opie.pie_sweep(zo, P["probe"], P["pos"], d, T, 0.9, order)
+    built = []
+    for C in (1, 2, 4, 8):
+        try:
+            ctx.set_cluster(tr, C)
+        except RuntimeError:
+            continue
+        built.append(C)
+        for form in (pft.LAUNCH_PER_COLOUR, pft.LAUNCH_DATAFLOW):
+            ctx.set_persistent(tr, form)
+            z = c64(P["init"], torch)
+            for _ in range(2):
+                ctx.iteration(z, tr, 0.9)
+            assert rel(z.cpu().numpy(), zo) < TOL, (C, form)
+    assert built[:3] == [1, 2, 4]
+    assert (8 in built) == ((n, M) in ((256, 16), (128, 32)))
+    with pytest.raises(RuntimeError):
+        ctx.set_cluster(tr, 3)
+    ctx.set_cluster(tr, 0)
+    ctx.close()

@@ -87,6 +87,7 @@ def test_null_and_invalid_arguments_are_refused_before_any_gpu_work(lib):
         lambda: lib.pie_ctx_colours(null, null, null),
         lambda: lib.pie_iteration(null, null, 0, 1.0, null, null),
         lambda: lib.pie_ctx_set_persistent(null, 0, 1),
+        lambda: lib.pie_ctx_set_cluster(null, 0, 4),
         lambda: lib.pie_ctx_set_order(null, null, 0),
         lambda: lib.pie_iteration_blind(null, null, 0, 1.0, 1.0, 0, null, null),
         lambda: lib.pie_iteration_blind(null, null, 0, 1.0, 1.0, 7, null, null),     # unknown probe step
