@@ -144,11 +144,11 @@ __device__ __forceinline__ void xbar_wait(uint32_t bar, uint32_t par, const PieA
   if (ok) return;
   unsigned long long t0, t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  while (true) {
+  for (unsigned spin = 1;; ++spin) {  // the error word is read every 16th try only
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
                  "selp.b32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(bar), "r"(par) : "memory");
     if (ok) return;
-    if (a.gerr && *reinterpret_cast<volatile int*>(a.gerr)) {
+    if ((spin & 15u) == 0u && a.gerr && *reinterpret_cast<volatile int*>(a.gerr)) {
       abort = true;
       return;
     }
@@ -240,11 +240,11 @@ __device__ __forceinline__ void wait_deps(const PieArgs& a, int s) {
       const unsigned* f = a.done + a.dep[i];
       unsigned long long t0, t;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-      while (true) {
+      for (unsigned spin = 1;; ++spin) {  // the error word is read every 16th poll only
         unsigned v;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
         if (v >= (unsigned)C + a.dep_extra) break;
-        if (*reinterpret_cast<volatile int*>(a.gerr)) {
+        if ((spin & 15u) == 0u && *reinterpret_cast<volatile int*>(a.gerr)) {
           ok = false;
           break;
         }
@@ -502,15 +502,46 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
     cp_async_commit();
     if constexpr (KEEP) {
       const int u = r0 + warp * G + g;
+      const float2* src = q.probe + u * N + Q * k;
+      if (Q % 2 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
 #pragma unroll
-      for (int l = 0; l < Q; ++l) wv[l] = __ldg(q.probe + u * N + Q * k + l);
+        for (int l = 0; l < Q; l += 2) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(src + l));
+          wv[l] = make_float2(t.x, t.y);
+          wv[l + 1] = make_float2(t.z, t.w);
+        }
+      } else {
+#pragma unroll
+        for (int l = 0; l < Q; ++l) wv[l] = __ldg(src + l);
+      }
     }
   };
   auto gather_obj = [&](const PieItem& q) {
     if constexpr (KEEP) {
       const int u = r0 + warp * G + g;
+      const float2* src = q.objr + q.obase + (long long)u * q.obj_w + Q * k;
+      // 16-byte loads where the lane's values allow (half the L1 wavefronts):
+      // all of them from a 16-byte boundary, else the inner Q - 2
+      if (Q % 2 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
 #pragma unroll
-      for (int l = 0; l < Q; ++l) zv[l] = __ldcg(q.objr + q.obase + (long long)u * q.obj_w + Q * k + l);
+        for (int l = 0; l < Q; l += 2) {
+          const float4 t = __ldcg(reinterpret_cast<const float4*>(src + l));
+          zv[l] = make_float2(t.x, t.y);
+          zv[l + 1] = make_float2(t.z, t.w);
+        }
+      } else if (Q % 2 == 0) {
+        zv[0] = __ldcg(src);
+#pragma unroll
+        for (int l = 1; l + 1 < Q; l += 2) {
+          const float4 t = __ldcg(reinterpret_cast<const float4*>(src + l));
+          zv[l] = make_float2(t.x, t.y);
+          zv[l + 1] = make_float2(t.z, t.w);
+        }
+        zv[Q - 1] = __ldcg(src + Q - 1);
+      } else {
+#pragma unroll
+        for (int l = 0; l < Q; ++l) zv[l] = __ldcg(src + l);
+      }
     }
   };
   const int step = gridDim.x / C;
@@ -703,6 +734,27 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
       const int ul = u0 + g, u = r0 + ul;
       float2 xv[Q];
       T::adjoint([&](int t) { return sG[ul * S::SG + t]; }, k, c.bh[1], sW2, net, xv);
+      if (KEEP && MODE == MODE_COLOURED && round == 0 && Q % 2 == 0) {  // 16-byte stores, as the loads
+        float2* dst = p.obj + obase + (long long)u * p.obj_w + Q * k;
+        float2 zn[Q];
+#pragma unroll
+        for (int l = 0; l < Q; ++l) {
+          const float2 d = cmulc(xv[l], wv[l]);  // conj(w) dpsi
+          zn[l] = make_float2(fmaf(-p.coef, d.x, zv[l].x), fmaf(-p.coef, d.y, zv[l].y));
+        }
+        if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+          for (int l = 0; l < Q; l += 2)
+            *reinterpret_cast<float4*>(dst + l) = make_float4(zn[l].x, zn[l].y, zn[l + 1].x, zn[l + 1].y);
+        } else {
+          dst[0] = zn[0];
+#pragma unroll
+          for (int l = 1; l + 1 < Q; l += 2)
+            *reinterpret_cast<float4*>(dst + l) = make_float4(zn[l].x, zn[l].y, zn[l + 1].x, zn[l + 1].y);
+          dst[Q - 1] = zn[Q - 1];
+        }
+        continue;
+      }
 #pragma unroll
       for (int l = 0; l < Q; ++l) {
         const int v = Q * k + l;
