@@ -639,6 +639,8 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
       CL::sync();
     }
     if (dyn && round == 0) claimed = *CL::map(&s_claim, 0u);
+    cp_async_wait_all();
+    __syncthreads();  // the amplitudes (fetched by every thread) are visible
     // 3a. columns (axis 1) of this CTA's slice (SPLIT: one column per warp,
     // its r terms split between the two 16-lane halves)
     if constexpr (SPLIT) {
@@ -664,22 +666,24 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
         T::forward(xv, k, c.bh[0], sW1, net, [&](int t1, float2 val) { sZ[t1 * S::ZS + tl] = val; });
       }
     }
-    cp_async_wait_all();
-    __syncthreads();
-    // 3b. modulus projection on the M x CM coefficients
-    ResAcc<MODE> part = 0;
-    for (int i = threadIdx.x; i < M * CM; i += NT) {
-      float2* z = sZ + (i / CM) * S::ZS + (i % CM);
-      *z = residual<MODE>(*z, sD[i], part);
-    }
-    warp_partial(round == 0 ? part : ResAcc<MODE>(0), sred);
-    __syncthreads();
+    // 3b. the modulus projection is applied as 3c loads the coefficients: the
+    // lane group that wrote a column in 3a reads it back, so a warp barrier
+    // suffices; only the group that stored an output adds its residual to the
+    // objective
+    __syncwarp();
+    ResAcc<MODE> part = 0, unused = 0;
+    const int w1 = T::first_out(k);
+    auto projected = [&](int t1, int tl) {
+      const int cc = (t1 - w1) / P;
+      const bool own = SPLIT ? (cc & 1) == g : SPLIT4 ? cc == g : true;
+      return residual<MODE>(sZ[t1 * S::ZS + tl], sD[t1 * CM + tl], own ? part : unused);
+    };
     // 3c. adjoint columns -> row owners (SPLIT: half g of the warp sends half
     // of each block; SPLIT4: group g computes and sends a quarter of it)
     if constexpr (SPLIT4) {
       for (int tl = warp; tl < CM; tl += NW) {
         float2 xq[Q / 4];
-        TS4::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, g, sBh, sW1, net, xq);
+        TS4::adjoint([&](int t1) { return projected(t1, tl); }, k, g, sBh, sW1, net, xq);
         const int u0 = Q * k + g * (Q / 4);
         const int tg = rank * CM + tl;
         if constexpr (XCH) {
@@ -699,9 +703,9 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
       const int tl = SPLIT ? cs0 : cs0 + g;
       float2 xv[Q];
       if constexpr (SPLIT)
-        TS::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, g, c.bh[0], sW1, net, xv);
+        TS::adjoint([&](int t1) { return projected(t1, tl); }, k, g, c.bh[0], sW1, net, xv);
       else
-        T::adjoint([&](int t1) { return sZ[t1 * S::ZS + tl]; }, k, c.bh[0], sW1, net, xv);
+        T::adjoint([&](int t1) { return projected(t1, tl); }, k, c.bh[0], sW1, net, xv);
       const int u0 = Q * k;
       const int tg = rank * CM + tl;
       constexpr int L0 = SPLIT ? Q / 2 : Q;  // values each lane sends
@@ -721,6 +725,8 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, P * Q, Q)) k_pie_p
         for (int l = 0; l < L0; ++l) dst[(u0 % RN + lb + l) * S::SG + tg] = xs[l];
       }
     }
+    warp_partial(round == 0 ? part : ResAcc<MODE>(0), sred);
+    __syncthreads();  // the warps' partial sums, read by thread 0 below
     if constexpr (XCH) {
       if (threadIdx.x == 0) xbar_expect(barG, (uint32_t)(8 * RN * M));  // every column of this CTA's rows
       xbar_wait(barG, parG, a, xabort);
@@ -960,46 +966,82 @@ __global__ void __launch_bounds__(NT, pie_min_blocks(MODE, C, N, 1)) k_pie_full(
       CL::sync();
     }
     if (dyn && round == 0) claimed = *CL::map(&s_claim, 0u);
-    // 3a. FFT of the local slot columns (rows in natural order -> slot order)
-    for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
-      const int b = b0 + g;
-      float2 x[E];
-#pragma unroll
-      for (int e = 0; e < E; ++e) x[e] = sC[(l + L * e) * S::SCS + b];
-      F::fwd(x, l, tw, net);
-#pragma unroll
-      for (int p = 0; p < E; ++p) sC[(p * L + l) * S::SCS + b] = x[p];
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    // 3b. modulus projection
     ResAcc<MODE> part = 0;
-    for (int i = threadIdx.x; i < N * CN; i += NT) {
-      float2* z = sC + (i / CN) * S::SCS + (i % CN);
-      *z = residual<MODE>(*z, sD[i], part);
-    }
-    warp_partial(round == 0 ? part : ResAcc<MODE>(0), sred);
-    __syncthreads();
-    // 3c. adjoint FFT of the local columns -> row owners (natural row order)
-    for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
-      const int b = b0 + g;
-      float2 x[E];
+    if constexpr (!CLAIM) {
+      // 3a-c. per warp, on its own columns and in registers: FFT of the local
+      // slot column (rows in natural order -> slot order), modulus projection,
+      // adjoint FFT (natural row order) -> row owners. Lane l of column b holds
+      // spectrum rows p L + l, whose amplitudes are sD[(p L + l) CN + b].
+      cp_async_wait_all();
+      __syncthreads();  // the amplitudes (fetched by every thread) are visible
+      for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
+        const int b = b0 + g;
+        float2 x[E];
 #pragma unroll
-      for (int p = 0; p < E; ++p) x[p] = sC[(p * L + l) * S::SCS + b];
-      F::adj(x, l, tw, net);
-      if constexpr (XCH) {
-        const uint32_t lr = smem_addr(sR);
+        for (int e = 0; e < E; ++e) x[e] = sC[(l + L * e) * S::SCS + b];
+        F::fwd(x, l, tw, net);
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int u = l + L * e;
-          const uint32_t r = (uint32_t)(u / RN);
-          st_async2(map_rank(lr + 8u * (uint32_t)((u % RN) * S::SRS + c0 + b), r), x[e], map_rank(barR, r));
+        for (int p = 0; p < E; ++p) x[p] = residual<MODE>(x[p], sD[(p * L + l) * CN + b], part);
+        F::adj(x, l, tw, net);
+        if constexpr (XCH) {
+          const uint32_t lr = smem_addr(sR);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int u = l + L * e;
+            const uint32_t r = (uint32_t)(u / RN);
+            st_async2(map_rank(lr + 8u * (uint32_t)((u % RN) * S::SRS + c0 + b), r), x[e], map_rank(barR, r));
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int u = l + L * e;
+            CL::map(sR, (unsigned)(u / RN))[(u % RN) * S::SRS + c0 + b] = x[e];
+          }
         }
-      } else {
+      }
+      warp_partial(round == 0 ? part : ResAcc<MODE>(0), sred);
+      __syncthreads();  // the warps' partial sums, read by thread 0 below
+    } else {  // the claiming variants keep the shared-memory round trip (registers)
+      // 3a. FFT of the local slot columns (rows in natural order -> slot order)
+      for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
+        const int b = b0 + g;
+        float2 x[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int u = l + L * e;
-          CL::map(sR, (unsigned)(u / RN))[(u % RN) * S::SRS + c0 + b] = x[e];
+        for (int e = 0; e < E; ++e) x[e] = sC[(l + L * e) * S::SCS + b];
+        F::fwd(x, l, tw, net);
+#pragma unroll
+        for (int p = 0; p < E; ++p) sC[(p * L + l) * S::SCS + b] = x[p];
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      // 3b. modulus projection
+      for (int i = threadIdx.x; i < N * CN; i += NT) {
+        float2* z = sC + (i / CN) * S::SCS + (i % CN);
+        *z = residual<MODE>(*z, sD[i], part);
+      }
+      warp_partial(round == 0 ? part : ResAcc<MODE>(0), sred);
+      __syncthreads();
+      // 3c. adjoint FFT of the local columns -> row owners (natural row order)
+      for (int b0 = warp * G; b0 < CN; b0 += NW * G) {
+        const int b = b0 + g;
+        float2 x[E];
+#pragma unroll
+        for (int p = 0; p < E; ++p) x[p] = sC[(p * L + l) * S::SCS + b];
+        F::adj(x, l, tw, net);
+        if constexpr (XCH) {
+          const uint32_t lr = smem_addr(sR);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int u = l + L * e;
+            const uint32_t r = (uint32_t)(u / RN);
+            st_async2(map_rank(lr + 8u * (uint32_t)((u % RN) * S::SRS + c0 + b), r), x[e], map_rank(barR, r));
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int u = l + L * e;
+            CL::map(sR, (unsigned)(u / RN))[(u % RN) * S::SRS + c0 + b] = x[e];
+          }
         }
       }
     }
