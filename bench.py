@@ -484,7 +484,12 @@ def main() -> None:
             "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, no measured SIMT peak)",
             "launches_per_sweep": {"pie_pft": kernel_launches(mode, ncol, tuning, "pft"),
                                    "pie_full": kernel_launches(mode, ncol, tuning, "full")},
-            "sweep_ms": {"pie_pft": k_pft_ms, "pie_full": k_full_ms}}
+            "sweep_ms": {"pie_pft": k_pft_ms, "pie_full": k_full_ms},
+            # both kernels of the step: the PFT sweep (the method's warm start) and the full-FFT
+            # refine sweep take about the same time, so either can be the dominant one
+            "per_kernel": {name: {"achieved": f / (ms / 1e3) / 1e12, "frac": f / (ms / 1e3) / 1e12 / peak,
+                                  "sweep_ms": ms, "flop_per_sweep": f, "traffic": _pie_traffic(name, len(P["pos"]))}
+                           for name, ms, f in (("pie_pft", k_pft_ms, f_pft), ("pie_full", k_full_ms, f_full))}}
 
     if rank == 0:
         cpu = None
@@ -638,14 +643,14 @@ def _csrc_sha(name: str) -> str:
 # writes are the L2's write-back of object lines. Valid only for the sources
 # hashed below (None otherwise).
 PIE_TRAFFIC = {
-    "pie_pft": {"sources": {"pie_kernels.cuh": "1e33f60d62c243867ee1b6c416eadca240b0b9af53f124e26dc7cb64afc2a862",
-                            "pft_core.cuh": "64b36f8b6ff3b2f453a06f28a26ee6ce1bbc559b067129de36559fc797c8b43f",
+    "pie_pft": {"sources": {"pie_kernels.cuh": "c6fd78e08ad5937fe3930ac35e722b8dbf30e8b287941b3424a0419ad513018f",
+                            "pft_core.cuh": "4dd7f88e185fb9abd29207f9e8515d7bb1917160fdc84c3f43ae88f59f125e14",
                             "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
-                "read_per_position": 5888 / 128, "write_per_position": 1143040 / 128},
-    "pie_full": {"sources": {"pie_kernels.cuh": "4c1d9a69170bdf40f5560292d9d84d2d0bfaaa72ff0277da60460241cc03699c",
+                "read_per_position": 3328 / 128, "write_per_position": 998144 / 128},
+    "pie_full": {"sources": {"pie_kernels.cuh": "c6fd78e08ad5937fe3930ac35e722b8dbf30e8b287941b3424a0419ad513018f",
                              "fft_core.cuh": "dd2552f57edd2220bfec6952833eeb81f9edcb4dd2d2b1e7f4bd407c1bbe064a",
                              "common.cuh": "c529d75cc0c99beb798916df141da403207dd42baf245cf975c1483736a558c3"},
-                 "read_per_position": 8490496 / 128, "write_per_position": 25600 / 128},
+                 "read_per_position": 8486144 / 128, "write_per_position": 27136 / 128},
 }
 
 
