@@ -53,15 +53,18 @@ constexpr uint32_t OFF_X = TAB_MAX;
 constexpr uint32_t OFF_TW = OFF_X + kStages * X_STAGE;
 constexpr uint32_t OFF_W = OFF_TW + 160 * 8;
 constexpr uint32_t OFF_XCH = OFF_W + kRt * kMl * 8;
-constexpr uint32_t OFF_PS = OFF_XCH + 2 * kRt * 32 * 8;
-constexpr uint32_t OFF_BAR = OFF_PS + 2 * kMl * 8;
+constexpr uint32_t OFF_PS = OFF_XCH + 4 * kRt * 32 * 8;  // two epilogue groups x two rows
+constexpr uint32_t OFF_BAR = OFF_PS + 4 * kMl * 8;
 constexpr int NBAR = 2 * kStages + 2 * kAccBufs + 1;
 constexpr uint32_t OFF_SLOT = OFF_BAR + 8 * NBAR;
 constexpr uint32_t OFF_ABORT = OFF_SLOT + 8;
 constexpr uint32_t SMEM_A = OFF_ABORT + 8;
 static_assert(SMEM_A <= 232448, "shared memory layout too large");
 
-constexpr int kEpiWarps = 4, kMmaWarp = 4, kLdWarp0 = 8, kLdWarps = 16;  // warps 5-7 idle
+// Two epilogue groups of four warps take alternate tiles (group 0: warps 0-3,
+// group 1: warps 8, 5, 6, 7, so that each group covers the four TMEM lane
+// quadrants, warp % 4); warp 4 issues the MMAs; warps 9-24 load.
+constexpr int kEpiWarps = 4, kMmaWarp = 4, kLdWarp0 = 9, kLdWarps = 16;
 constexpr int kThreadsA = 32 * (kLdWarp0 + kLdWarps);
 constexpr int kRowsPerThread = 128 / (2 * kLdWarps);  // 4
 constexpr uint32_t TMEM_COLS = 128;
@@ -215,24 +218,27 @@ __global__ void __launch_bounds__(kThreadsA, 1)
       mbar_wait(DONE, 0, &never, kWaitNs);
     }
     __syncwarp();
-  } else if (warp < kEpiWarps) {
+  } else if (warp < kLdWarp0) {
     // TMEM lane m = 32 q + lane: block k = 32 h + lane of row r = q >> 1
     // (h = q & 1). Warp h = 0 of a row runs the FFTs of j = 0..6, warp h = 1
     // those of j = 7..12; each first hands the other the half of C it lacks.
-    const int q = warp, r = q >> 1, h = q & 1;
+    // Group g takes tiles g, g + 2, ...
+    const int grp = warp < kEpiWarps ? 0 : 1;
+    const int q = warp % 4, r = q >> 1, h = q & 1;
+    const int pid = 1 + 2 * grp + r;  // named barrier of the row's warp pair
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     constexpr int kJ0 = 7;
     const int jlo = h ? kJ0 : 0, jhi = h ? kRt : kJ0;
-    float2* xch = reinterpret_cast<float2*>(sm + OFF_XCH) + r * kRt * 32;
-    float2* ps = reinterpret_cast<float2*>(sm + OFF_PS) + r * kMl;
+    float2* xch = reinterpret_cast<float2*>(sm + OFF_XCH) + (2 * grp + r) * kRt * 32;
+    float2* ps = reinterpret_cast<float2*>(sm + OFF_PS) + (2 * grp + r) * kMl;
     typename F64::Net net;
     F64::init_net(net, lane, s_tw);
-    for (long long T = 0; T < ntiles; ++T) {
+    for (long long T = grp; T < ntiles; T += 2) {
       const long long tile = blockIdx.x + T * gridDim.x;
       const int b = (int)(T % kAccBufs);
       const uint32_t v = (uint32_t)(T / kAccBufs);
       const bool got = mbar_wait(ACC_FULL + 8 * b, v & 1u, abort_flag, kWaitNs);
-      if (!pair_all(got, 1 + r)) break;
+      if (!pair_all(got, pid)) break;
       tc_fence_after();
       float re[16], im[16];
       tmem_ld16(tmem + lane_off + b * ACC_COLS, re);
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(kThreadsA, 1)
 #pragma unroll
       for (int j = 0; j < kRt; ++j)
         if (j < jlo || j >= jhi) xch[j * 32 + lane] = make_float2(re[j], im[j]);
-      pair_barrier(1 + r);
+      pair_barrier(pid);
       float2 acc[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(kThreadsA, 1)
 #pragma unroll
         for (int i = 0; i < 4; ++i) ps[i * 32 + lane] = acc[i];
       }
-      pair_barrier(1 + r);
+      pair_barrier(pid);
       if (!h) {
         const long long row = 2 * tile + r;
         const long long f = row / rows_per_frame;
@@ -414,8 +420,12 @@ constexpr uint32_t OFF2_SLOT = OFF2_BAR + 8 * NBAR2;
 constexpr uint32_t OFF2_ABORT = OFF2_SLOT + 8;
 constexpr uint32_t SMEM_E = OFF2_ABORT + 8;
 static_assert(SMEM_E <= 232448, "shared memory layout too large");
-constexpr int kLdWarpsE = 4, kLdWarp0E = 8;
-constexpr int kThreadsE = 32 * (kLdWarp0E + kLdWarpsE);  // warps 5-7 idle
+// Loader warps: three groups of four (warps 8-19) that take every third tile,
+// each filling the operand stage of its tile (warps 5-7 idle). At small q the
+// stage-B adjoint of a tile's two rows costs more than its expansion, so more
+// groups keep the tensor cores and the stores fed.
+constexpr int kLdWarpsE = 4, kLdWarp0E = 8, kLdGroupsE = 3;
+constexpr int kThreadsE = 32 * (kLdWarp0E + kLdGroupsE * kLdWarpsE);
 
 __device__ __forceinline__ void split8_store(uint8_t* hi_base, uint32_t comp_bytes, uint32_t off, const float (&v)[8]) {
   __nv_bfloat162 h[4], l[4];
@@ -556,11 +566,12 @@ __global__ void __launch_bounds__(kThreadsE, 1)
   } else if (warp >= kLdWarp0E) {
     // warp pair per row r of the tile; warp h fills the K core-matrix column
     // j = 8h .. 8h + 7 of blocks k = lane and lane + 32 (terms j >= 13 are 0)
-    const int w = warp - kLdWarp0E, r = w >> 1, h = w & 1;
+    const int grp = (warp - kLdWarp0E) / kLdWarpsE;
+    const int w = (warp - kLdWarp0E) % kLdWarpsE, r = w >> 1, h = w & 1;
     typename F64::Net net;
     F64::init_net(net, lane, s_tw);
     const int rho0 = 2 * bitrev<32>(lane);
-    for (long long T = 0; T < ntiles; ++T) {
+    for (long long T = grp; T < ntiles; T += kLdGroupsE) {
       const long long tile = blockIdx.x + T * gridDim.x;
       const int s = (int)(T % kStagesE);
       const uint32_t u = (uint32_t)(T / kStagesE);
